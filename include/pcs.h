@@ -1,0 +1,170 @@
+/*
+ * pcs.h -- C ABI of libpcs: GB300 (sm_103a) primal-dual reconstruction for
+ * susceptibility-based positive-contrast MRI.
+ *
+ * The library solves, independently for every 2-D slice s of a stack,
+ *
+ *     chi_s = argmin  lambda/2 || W (D chi - dB) ||_2^2 + || M G chi ||_1      (Eq. (1))
+ *
+ * with the first-order primal-dual (Chambolle-Pock) iteration of the paper's
+ * Sec. II.A pseudocode: zero start, then N times
+ *
+ *     p    <- (p + sigma (W D chibar - W dB)) / (1 + sigma/lambda)     dual data prox
+ *     q    <- clamp(q + sigma M G chibar, -1, 1)                        dual TV prox
+ *     chi+ <- chi - tau D W p - tau G^T M q                             primal step
+ *     chibar <- 2 chi+ - chi;  chi <- chi+                              over-relaxation
+ *
+ * Conventions (readings of the paper, which leaves them open):
+ *   - slices are H x W, row-major, stacked as [S][H][W]; row index i runs
+ *     along y, column index j along x;
+ *   - D is the dipole convolution F^-1 D(k) F with D(k) = 1/3 - k_par^2/|k|^2,
+ *     D(0) = 0, circular on the slice; B0 lies in-plane along y (rows) unless
+ *     pcs_options.b0_axis = 1 (columns);
+ *   - G is forward differences with a Neumann boundary; G^T its exact adjoint;
+ *   - W = M = mask (0/1); the TV dual prox is the componentwise clamp;
+ *   - the primal function is zero, so the primal prox is the identity;
+ *   - the iteration count N is fixed and the output is chi_N.
+ *
+ * All arithmetic of the iteration runs in FP32 on the GPU; the step sizes and
+ * kernel tables are computed in FP64 on the host and rounded once.
+ *
+ * Ownership: the caller owns every input and output buffer and every stream.
+ * The library owns its context, its scratch (dual variables, chibar, device
+ * tables) and never frees or retains caller memory.  Work is enqueued on the
+ * context's stream; functions return after enqueueing unless stated
+ * otherwise.  Errors are reported as pcs_status codes only; nothing aborts or
+ * throws across this boundary.  pcs_last_error() gives a thread-local text.
+ */
+#ifndef PCS_H
+#define PCS_H
+
+#include <stddef.h>
+
+/* Only the functions below are exported from libpcs.so. */
+#if defined(__GNUC__)
+#define PCS_API __attribute__((visibility("default")))
+#else
+#define PCS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcs_ctx pcs_ctx; /* opaque */
+
+typedef enum pcs_status {
+    PCS_OK = 0,
+    PCS_EINVAL = 1,       /* bad argument: NULL pointer, non-positive lambda/tau/sigma, S > max_slices ... */
+    PCS_EUNSUPPORTED = 2, /* slice size without a compiled kernel (see pcs_supported_size) */
+    PCS_ENOMEM = 3,       /* device allocation failed */
+    PCS_ECUDA = 4,        /* a CUDA runtime call failed (no device, launch failure, ...) */
+    PCS_ETIMEOUT = 5,     /* a bounded device wait expired (reserved; no current kernel waits) */
+    PCS_EBUSY = 6         /* context in use by another call */
+} pcs_status;
+
+typedef struct pcs_options {
+    int b0_axis;       /* 0 = B0 along rows / y (default), 1 = along columns / x */
+    int cluster_size;  /* 0 = library default for the slice size; else CTAs per slice (1,2,4,8,16) */
+    int max_clusters;  /* 0 = as many concurrent clusters as fit; else an upper bound (tuning) */
+    int reserved[5];
+} pcs_options;
+
+/* Diagnostics of one slice at (chi_N, p_N, q_N), in FP64 (see pcs_slice_report doc below). */
+typedef struct pcs_slice_report {
+    double objective;     /* lambda/2 ||W(D chi - dB)||^2 + ||M G chi||_1 (Eq. (1)) */
+    double gap;           /* Fenchel-Young gap: ||p - lambda(W D chi - W dB)||^2/(2 lambda)
+                             + sum(|g| - q.g), g = M G chi; >= 0 */
+    double stationarity;  /* || D W p + G^T M q ||_2 */
+    double data_residual; /* || W (D chi - dB) ||_2 */
+    int iters;
+    int pad;
+} pcs_slice_report;
+
+/* Fill *opt with the defaults (all zero). Returns PCS_EINVAL if opt is NULL. */
+PCS_API pcs_status pcs_options_default(pcs_options *opt);
+
+/* Non-zero if H x W slices have a compiled kernel in this build. */
+PCS_API int pcs_supported_size(int H, int W);
+
+/*
+ * Create a context for slices of H x W and batches of up to max_slices.
+ * Computes the dipole-kernel table D(k) (Eq. (1)'s D, with D(0) = 0) and the
+ * FFT twiddles in FP64 on the host, uploads them, and allocates the scratch
+ * state (chibar, p, qx, qy: 4 x max_slices x H x W floats).
+ *   out         receives the context (set to NULL on failure)
+ *   opt         NULL for defaults
+ *   cuda_stream a cudaStream_t (NULL = legacy default stream) used by every
+ *               later call on this context
+ * Errors: PCS_EINVAL (out NULL, max_slices < 1), PCS_EUNSUPPORTED (size),
+ *         PCS_ECUDA (no device), PCS_ENOMEM.
+ */
+PCS_API pcs_status pcs_create(pcs_ctx **out, int H, int W, int max_slices, const pcs_options *opt,
+                      void *cuda_stream);
+
+/* Change the stream later calls enqueue on. */
+PCS_API pcs_status pcs_set_stream(pcs_ctx *ctx, void *cuda_stream);
+
+/*
+ * Run n_iter primal-dual iterations (Sec. II.A pseudocode) on S independent
+ * slices and write chi_N.
+ *   field   device, [S][H][W] float32: the normalised local field dB/B0 (ppm)
+ *   mask    device, [S][H][W] uint8 0/1: W = M = mask
+ *   lambda  regularisation weight of Eq. (1), > 0
+ *   tau, sigma  primal and dual steps, > 0 (the paper uses tau = sigma = 1/||K||;
+ *               see pcs_opnorm); tau*sigma*||K||^2 <= 1 is the caller's duty
+ *   n_iter  >= 0 (0 gives chi = 0)
+ *   chi_out device, [S][H][W] float32, caller-owned; also serves as the
+ *           primal iterate during the solve (must not alias field)
+ *   rep     NULL, or a host array of S reports; when given, the call also
+ *           evaluates the FP64 diagnostics and synchronises the stream
+ * All device pointers must be 16-byte aligned.  Slices are independent: the
+ * result for a slice does not depend on the other slices in the call.
+ * Errors: PCS_EINVAL, PCS_ECUDA.
+ */
+PCS_API pcs_status pcs_solve_slices(pcs_ctx *ctx, const float *field, const unsigned char *mask, int S,
+                            double lambda, double tau, double sigma, int n_iter, float *chi_out,
+                            pcs_slice_report *rep);
+
+/*
+ * Same as pcs_solve_slices, but field, mask and chi_out are HOST buffers
+ * (pinned memory gives full copy bandwidth).  Copies the inputs to
+ * library-owned device staging buffers, solves, copies chi back and
+ * synchronises the stream before returning.  This is the Sec. II.B flow:
+ * one host-to-device copy in, one device-to-host copy out.
+ */
+PCS_API pcs_status pcs_solve_slices_host(pcs_ctx *ctx, const float *field_host,
+                                 const unsigned char *mask_host, int S, double lambda, double tau,
+                                 double sigma, int n_iter, float *chi_out_host,
+                                 pcs_slice_report *rep);
+
+/*
+ * FP64 diagnostics of the state left by the last pcs_solve_slices on this
+ * context (chi is the caller's chi_out of that call): objective, Fenchel-Young
+ * gap, stationarity and data residual per slice (pcs_slice_report).  Runs
+ * two extra dipole convolutions per slice on the GPU with FP64 reductions
+ * and synchronises the stream.  rep: host array of S entries.
+ */
+PCS_API pcs_status pcs_report(pcs_ctx *ctx, const float *field, const unsigned char *mask, int S,
+                      double lambda, const float *chi, pcs_slice_report *rep);
+
+/*
+ * L = ||K||_2 for K = [W D; M G] of each slice's mask, by power iteration on
+ * K^T K (pseudocode step 1), power_iters iterations from a fixed
+ * pseudo-random start.  mask: device [S][H][W] uint8; L_out: host array [S].
+ * Synchronises the stream.
+ */
+PCS_API pcs_status pcs_opnorm(pcs_ctx *ctx, const unsigned char *mask, int S, int power_iters,
+                      double *L_out);
+
+/* Release the context and everything it owns. NULL-safe. */
+PCS_API void pcs_destroy(pcs_ctx *ctx);
+
+/* Thread-local text of the last error on this thread ("" if none). */
+PCS_API const char *pcs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCS_H */

@@ -1,0 +1,242 @@
+"""Python binding of libpcs (GB300 primal-dual positive-contrast susceptibility solver).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of
+``libpcs.so`` (built from ``csrc/`` by ``build.py``).  The functions keep the
+C names of ``include/pcs.h`` and take torch tensors (device memory) or numpy
+arrays (host memory); PyTorch is used only for device memory and streams.
+There is no CPU fallback: if the library is missing, importing works but the
+first call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpcs.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "pcs.h")
+
+PCS_OK, PCS_EINVAL, PCS_EUNSUPPORTED, PCS_ENOMEM, PCS_ECUDA, PCS_ETIMEOUT, PCS_EBUSY = range(7)
+STATUS_NAMES = ["PCS_OK", "PCS_EINVAL", "PCS_EUNSUPPORTED", "PCS_ENOMEM", "PCS_ECUDA", "PCS_ETIMEOUT", "PCS_EBUSY"]
+
+
+class PcsError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}: {message}")
+
+
+class pcs_options(ctypes.Structure):
+    _fields_ = [
+        ("b0_axis", ctypes.c_int),
+        ("cluster_size", ctypes.c_int),
+        ("max_clusters", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
+    ]
+
+
+class pcs_slice_report(ctypes.Structure):
+    _fields_ = [
+        ("objective", ctypes.c_double),
+        ("gap", ctypes.c_double),
+        ("stationarity", ctypes.c_double),
+        ("data_residual", ctypes.c_double),
+        ("iters", ctypes.c_int),
+        ("pad", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in ("objective", "gap", "stationarity", "data_residual", "iters")}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpcs.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"libpcs.so not found at {path}: build it first "
+            "(python -c 'import __graft_entry__ as g; g.build()')"
+        )
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "pcs_options_default": (i, [ctypes.POINTER(pcs_options)]),
+        "pcs_supported_size": (i, [i, i]),
+        "pcs_create": (i, [ctypes.POINTER(vp), i, i, i, ctypes.POINTER(pcs_options), vp]),
+        "pcs_set_stream": (i, [vp, vp]),
+        "pcs_solve_slices": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
+        "pcs_solve_slices_host": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
+        "pcs_report": (i, [vp, vp, vp, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
+        "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
+        "pcs_destroy": (None, [vp]),
+        "pcs_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions include/pcs.h declares."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcs_[a-z_0-9]+)\s*\(", text)))
+
+
+def last_error() -> str:
+    return load_library().pcs_last_error().decode()
+
+
+def _check(status: int, where: str):
+    if status != PCS_OK:
+        raise PcsError(status, where, last_error())
+
+
+def _dev_ptr(t, dtype_name: str, shape, what: str):
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be on a CUDA device")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"{what} must be {dtype_name}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype, shape, what: str):
+    import numpy as np
+
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or tuple(a.shape) != tuple(shape):
+        raise TypeError(f"{what} must be a numpy {np.dtype(dtype).name} array of shape {tuple(shape)}")
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{what} must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# --------------------------------------------------------------------------- C-named wrappers
+
+
+def pcs_supported_size(H: int, W: int) -> bool:
+    return bool(load_library().pcs_supported_size(H, W))
+
+
+def pcs_create(H: int, W: int, max_slices: int, b0_axis: int = 0, cluster_size: int = 0, max_clusters: int = 0,
+               stream=None):
+    """Create a context; returns an opaque handle (c_void_p).  stream: torch.cuda.Stream or None (current)."""
+    import torch
+
+    lib = load_library()
+    opt = pcs_options()
+    lib.pcs_options_default(ctypes.byref(opt))
+    opt.b0_axis, opt.cluster_size, opt.max_clusters = b0_axis, cluster_size, max_clusters
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    h = ctypes.c_void_p()
+    _check(lib.pcs_create(ctypes.byref(h), H, W, max_slices, ctypes.byref(opt), ctypes.c_void_p(s)), "pcs_create")
+    return h
+
+
+def pcs_set_stream(ctx, stream):
+    _check(load_library().pcs_set_stream(ctx, ctypes.c_void_p(stream.cuda_stream)), "pcs_set_stream")
+
+
+def pcs_solve_slices(ctx, field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, report=False):
+    """Solve every slice of field/mask ([S][H][W] float32 / uint8 CUDA tensors) into chi_out."""
+    S, H, W = field.shape
+    f = _dev_ptr(field, "float32", (S, H, W), "field")
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
+    rep = (pcs_slice_report * S)() if report and S > 0 else None
+    _check(load_library().pcs_solve_slices(ctx, f, m, S, lam, tau, sigma, n_iter, c, rep), "pcs_solve_slices")
+    return [r.as_dict() for r in rep] if rep is not None else None
+
+
+def pcs_solve_slices_host(ctx, field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, report=False):
+    """Host-buffer variant: numpy arrays in (pinned or pageable), chi_out numpy array filled on return."""
+    import numpy as np
+
+    S, H, W = field.shape
+    f = _host_ptr(field, np.float32, (S, H, W), "field")
+    m = _host_ptr(mask, np.uint8, (S, H, W), "mask")
+    c = _host_ptr(chi_out, np.float32, (S, H, W), "chi_out")
+    rep = (pcs_slice_report * S)() if report and S > 0 else None
+    _check(load_library().pcs_solve_slices_host(ctx, f, m, S, lam, tau, sigma, n_iter, c, rep),
+           "pcs_solve_slices_host")
+    return [r.as_dict() for r in rep] if rep is not None else None
+
+
+def pcs_report(ctx, field, mask, lam: float, chi):
+    S, H, W = field.shape
+    f = _dev_ptr(field, "float32", (S, H, W), "field")
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    c = _dev_ptr(chi, "float32", (S, H, W), "chi")
+    rep = (pcs_slice_report * S)()
+    _check(load_library().pcs_report(ctx, f, m, S, lam, c, rep), "pcs_report")
+    return [r.as_dict() for r in rep]
+
+
+def pcs_opnorm(ctx, mask, power_iters: int = 200):
+    S, H, W = mask.shape
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    out = (ctypes.c_double * S)()
+    _check(load_library().pcs_opnorm(ctx, m, S, power_iters, out), "pcs_opnorm")
+    return list(out)
+
+
+def pcs_destroy(ctx):
+    if ctx is not None:
+        load_library().pcs_destroy(ctx)
+
+
+class Solver:
+    """Owns one context: ``with Solver(H, W, S) as s: s.solve(field, mask, lam, n_iter)``."""
+
+    def __init__(self, H: int, W: int, max_slices: int, **opts):
+        self.H, self.W, self.max_slices = H, W, max_slices
+        self.ctx = pcs_create(H, W, max_slices, **opts)
+        self._L = None
+
+    def step_sizes(self, power_iters: int = 300):
+        """(L, tau, sigma) with tau = sigma = 1/L for the full-mask operator of this slice size."""
+        import torch
+
+        if self._L is None:
+            ones = torch.ones((1, self.H, self.W), dtype=torch.uint8, device="cuda")
+            self._L = pcs_opnorm(self.ctx, ones, power_iters)[0]
+        return self._L, 1.0 / self._L, 1.0 / self._L
+
+    def solve(self, field, mask, lam: float, n_iter: int, tau: float | None = None, sigma: float | None = None,
+              chi_out=None, report=False):
+        import torch
+
+        if tau is None or sigma is None:
+            _, tau, sigma = self.step_sizes()
+        if chi_out is None:
+            chi_out = torch.empty_like(field)
+        rep = pcs_solve_slices(self.ctx, field, mask, lam, tau, sigma, n_iter, chi_out, report=report)
+        return (chi_out, rep) if report else chi_out
+
+    def close(self):
+        pcs_destroy(self.ctx)
+        self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,227 @@
+// fft_core.cuh -- warp-group complex FFT engine for the dipole convolution.
+//
+// One 1-D transform of length N is carried by a group of T lanes of one warp
+// (T <= 32), E = N / T complex elements per lane.  Register order: lane g of
+// the group holds element  g + T*e  in x[e], both on input (natural order) and
+// on output (natural-order spectrum).  That shared order is what lets the
+// solver fuse its pointwise steps between an inverse and a forward transform
+// without moving data.
+//
+// The transform is a Stockham autosort radix-R factorisation (radices 16, 8,
+// 4, 2): each stage reads its butterfly inputs at stride N/R, applies the
+// twiddles W_{Ns R}^{r k}, a register DFT_R, and writes to the next stage's
+// natural position; the group exchanges through a padded shared-memory
+// buffer between stages.  Padding: element i lives at P(i) = i + i/16 (one
+// 8-byte word per 16), which keeps the strided stores of a stage on distinct
+// banks.
+//
+// Twiddles come from a table tw[m] = exp(-2 pi i m / NTW) (host FP64,
+// rounded to FP32) held in shared memory; a transform of length N uses every
+// (NTW/N)-th entry (TWS = NTW / N).  Inverse transforms use conjugates and
+// are unnormalised.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pcs {
+
+__device__ __forceinline__ int P(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// multiply by the constant (c, s) with s given for the forward sign; INV flips it
+template <bool INV>
+__device__ __forceinline__ float2 mul_const(float2 a, float c, float s) {
+    const float ss = INV ? -s : s;
+    return make_float2(fmaf(a.x, c, -a.y * ss), fmaf(a.x, ss, a.y * c));
+}
+
+// cos / sin of 2*pi*k/16 (forward twiddles are (cos, -sin))
+constexpr float kC1 = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kS1 = 0.38268343236508977173f;  // sin(pi/8)
+constexpr float kR2 = 0.70710678118654752440f;  // sqrt(1/2)
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    const float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+    const float2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
+    const float2 t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
+    v0 = cadd(t0, t2);
+    v2 = csub(t0, t2);
+    v1 = cadd(t1, t3);
+    v3 = csub(t1, t3);
+}
+
+// in-place, natural order in and out
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = mul_const<INV>(o1, kR2, -kR2);
+    o2 = mul_mi<INV>(o2);
+    o3 = mul_const<INV>(o3, -kR2, -kR2);
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+    float2 e[8], o[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        e[t] = v[2 * t];
+        o[t] = v[2 * t + 1];
+    }
+    dft8<INV>(e);
+    dft8<INV>(o);
+    // W16^k = (cos(2 pi k/16), -sin(2 pi k/16)) forward
+    o[1] = mul_const<INV>(o[1], kC1, -kS1);
+    o[2] = mul_const<INV>(o[2], kR2, -kR2);
+    o[3] = mul_const<INV>(o[3], kS1, -kC1);
+    o[4] = mul_mi<INV>(o[4]);
+    o[5] = mul_const<INV>(o[5], -kS1, -kC1);
+    o[6] = mul_const<INV>(o[6], -kR2, -kR2);
+    o[7] = mul_const<INV>(o[7], -kC1, -kS1);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        v[t] = cadd(e[t], o[t]);
+        v[t + 8] = csub(e[t], o[t]);
+    }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dftR(float2 (&v)[R]) {
+    if constexpr (R == 2) {
+        dft2<INV>(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 8) {
+        dft8<INV>(v);
+    } else {
+        static_assert(R == 16, "radix");
+        dft16<INV>(v);
+    }
+}
+
+// Radix plans: R1 first, RL last, RM middle (0 = two stages only).
+template <int N, int E>
+struct Plan;
+template <> struct Plan<32, 8>   { static constexpr int R1 = 8,  RM = 0,  RL = 4; };
+template <> struct Plan<64, 8>   { static constexpr int R1 = 8,  RM = 0,  RL = 8; };
+template <> struct Plan<128, 16> { static constexpr int R1 = 16, RM = 0,  RL = 8; };
+template <> struct Plan<256, 16> { static constexpr int R1 = 16, RM = 0,  RL = 16; };
+template <> struct Plan<512, 16> { static constexpr int R1 = 16, RM = 16, RL = 2; };
+
+// Twiddle the legs of one butterfly of a stage with span NS and radix R.
+template <int N, int R, int NS, bool INV, int TWS>
+__device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __restrict__ tw) {
+    if constexpr (NS > 1) {
+        const int k = j & (NS - 1);
+        constexpr int STEP = N / (NS * R);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            float2 w = tw[(r * k * STEP) * TWS];
+            if (INV) w.y = -w.y;
+            v[r] = cmul(v[r], w);
+        }
+    }
+}
+
+// Complex FFT of length N by a group of T lanes (lane g, group mask gm).
+// x: E = N/T elements, element g + T*e in x[e]; buf: group-private padded
+// buffer of P(N-1)+1 entries (contents destroyed).
+template <int N, int T, bool INV, int TWS>
+__device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf,
+                                    const float2* __restrict__ tw, int g, unsigned gm) {
+    constexpr int E = N / T;
+    using PL = Plan<N, E>;
+    constexpr int R1 = PL::R1, RM = PL::RM, RL = PL::RL;
+    static_assert(E % R1 == 0 && E % RL == 0, "plan");
+    static_assert(R1 * (RM ? RM : 1) * RL == N, "plan product");
+
+    __syncwarp(gm);
+    // ---- stage 1: radix R1, span 1, inputs from registers
+    {
+        constexpr int B = E / R1;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            float2 v[R1];
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v[r] = x[b + r * B];
+            dftR<R1, INV>(v);
+            const int j = g + b * T;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) buf[P(j * R1 + r)] = v[r];
+        }
+    }
+    __syncwarp(gm);
+    // ---- optional middle stage: radix RM, span R1, in place through registers
+    if constexpr (RM != 0) {
+        constexpr int B = E / RM;
+        constexpr int NS = R1;
+        float2 v[B][RM];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int j = g + b * T;
+#pragma unroll
+            for (int r = 0; r < RM; ++r) v[b][r] = buf[P(j + r * (N / RM))];
+        }
+        __syncwarp(gm);
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int j = g + b * T;
+            twiddle<N, RM, NS, INV, TWS>(v[b], j, tw);
+            dftR<RM, INV>(v[b]);
+            const int k = j & (NS - 1);
+            const int base = (j / NS) * NS * RM + k;
+#pragma unroll
+            for (int r = 0; r < RM; ++r) buf[P(base + r * NS)] = v[b][r];
+        }
+        __syncwarp(gm);
+    }
+    // ---- last stage: radix RL, span N/RL, outputs to registers (natural order)
+    {
+        constexpr int B = E / RL;
+        constexpr int NS = N / RL;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int j = g + b * T;
+            float2 v[RL];
+#pragma unroll
+            for (int r = 0; r < RL; ++r) v[r] = buf[P(j + r * NS)];
+            twiddle<N, RL, NS, INV, TWS>(v, j, tw);
+            dftR<RL, INV>(v);
+#pragma unroll
+            for (int r = 0; r < RL; ++r) x[b + r * B] = v[r];
+        }
+    }
+    __syncwarp(gm);
+}
+
+}  // namespace pcs

@@ -1,0 +1,429 @@
+// pcs_api.cu -- the C ABI of libpcs (declared in include/pcs.h).
+//
+// Host side of the solver: argument validation, the FP64 dipole-kernel and
+// twiddle tables, context-owned scratch, kernel variant selection and launch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pcs.h"
+#include "pd_launch.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pcs_status fail(pcs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+pcs_status cuda_fail(cudaError_t e, const char* what) {
+    pcs_status st = (e == cudaErrorMemoryAllocation) ? PCS_ENOMEM : PCS_ECUDA;
+    return fail(st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define PCS_CUDA(call, what)                         \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+std::vector<pcs::KernelEntry> all_entries() {
+    std::vector<pcs::KernelEntry> v;
+    const pcs::KernelEntry* (*fns[])(int*) = {pcs::entries_64, pcs::entries_128, pcs::entries_256,
+                                               pcs::entries_512};
+    for (auto fn : fns) {
+        int n = 0;
+        const pcs::KernelEntry* e = fn(&n);
+        for (int k = 0; k < n; ++k) v.push_back(e[k]);
+    }
+    return v;
+}
+
+const std::vector<pcs::KernelEntry>& entries() {
+    static const std::vector<pcs::KernelEntry> v = all_entries();
+    return v;
+}
+
+// First entry for (H, W) is the default; cluster_size > 0 selects a variant.
+const pcs::KernelEntry* find_entry(int H, int W, int cluster_size) {
+    for (const auto& e : entries())
+        if (e.H == H && e.W == W && (cluster_size <= 0 || e.C == cluster_size)) return &e;
+    return nullptr;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ tables (FP64 on the host)
+
+namespace pcs {
+
+// D(k) = 1/3 - k_par^2/|k|^2 with D(0) = 0 on the FFT grid (Eq. (1)'s dipole
+// kernel), laid out for the column pass: dtab[kx][ky], kx in [0, W/2), every
+// entry divided by H*W (the unnormalised transforms' scale).  Column kx = 0
+// holds Dm = (D(ky,0) + D(ky,W/2))/2 and ddtab[ky] = (D(ky,0) - D(ky,W/2))/2,
+// the two halves of the packed DC/Nyquist column.
+void build_dipole_tables(int H, int W, int b0_axis, std::vector<float>& dtab, std::vector<float>& ddtab) {
+    const int M = W / 2;
+    auto freq = [](int idx, int n) {  // cycles per pixel, numpy.fft.fftfreq convention
+        return (idx < (n + 1) / 2) ? (double)idx / n : (double)(idx - n) / n;
+    };
+    auto D = [&](int ky_idx, int kx_idx) {
+        const double ky = freq(ky_idx, H), kx = freq(kx_idx, W);
+        const double k2 = kx * kx + ky * ky;
+        if (k2 == 0.0) return 0.0;
+        const double kp = (b0_axis == 0) ? ky : kx;
+        return 1.0 / 3.0 - kp * kp / k2;
+    };
+    const double scale = 1.0 / ((double)H * (double)W);
+    dtab.assign((size_t)M * H, 0.f);
+    ddtab.assign((size_t)H, 0.f);
+    for (int kx = 0; kx < M; ++kx)
+        for (int ky = 0; ky < H; ++ky) dtab[(size_t)kx * H + ky] = (float)(D(ky, kx) * scale);
+    for (int ky = 0; ky < H; ++ky) {
+        const double d0 = D(ky, 0), d1 = D(ky, M);
+        dtab[ky] = (float)(0.5 * (d0 + d1) * scale);
+        ddtab[ky] = (float)(0.5 * (d0 - d1) * scale);
+    }
+}
+
+// tw[m] = exp(-2 pi i m / n), m in [0, n)
+void build_twiddles(int n, std::vector<float2>& tw) {
+    tw.resize(n);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int m = 0; m < n; ++m) {
+        const double a = two_pi * (double)m / (double)n;
+        tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+}
+
+}  // namespace pcs
+
+// ------------------------------------------------------------------ context
+
+struct pcs_ctx {
+    int H = 0, W = 0, max_slices = 0;
+    pcs_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    const pcs::KernelEntry* entry = nullptr;
+    int max_clusters = 0;
+    int max_clusters_aux = 0;
+    int last_iters = 0;
+    // device tables
+    float* dtab = nullptr;
+    float* ddtab = nullptr;
+    float2* twid = nullptr;
+    // scratch state
+    float* chibar = nullptr;
+    float* p = nullptr;
+    float* qx = nullptr;
+    float* qy = nullptr;
+    // staging for the host-buffer entry point (allocated on first use)
+    float* st_field = nullptr;
+    unsigned char* st_mask = nullptr;
+    float* st_chi = nullptr;
+    // diagnostics / power iteration (allocated on first use)
+    double* partials = nullptr;
+    double* Ldev = nullptr;
+    float* xa = nullptr;
+    float* xb = nullptr;
+    std::mutex mu;
+};
+
+namespace {
+
+void free_ctx(pcs_ctx* c) {
+    if (!c) return;
+    void* ptrs[] = {c->dtab,     c->ddtab,  c->twid,    c->chibar, c->p,   c->qx,  c->qy,
+                    c->st_field, c->st_mask, c->st_chi, c->partials, c->Ldev, c->xa, c->xb};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete c;
+}
+
+size_t slice_elems(const pcs_ctx* c) { return (size_t)c->H * (size_t)c->W; }
+
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+pcs_status validate_solve(pcs_ctx* ctx, const void* field, const void* mask, int S, double lambda, double tau,
+                          double sigma, int n_iter, const void* chi_out) {
+    if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
+    if (S < 0 || S > ctx->max_slices) return fail(PCS_EINVAL, "S=%d outside [0, max_slices=%d]", S, ctx->max_slices);
+    if (S == 0) return PCS_OK;
+    if (!field || !mask || !chi_out) return fail(PCS_EINVAL, "NULL field/mask/chi_out");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(PCS_EINVAL, "lambda must be > 0 (got %g)", lambda);
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(PCS_EINVAL, "tau must be > 0 (got %g)", tau);
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(PCS_EINVAL, "sigma must be > 0 (got %g)", sigma);
+    if (n_iter < 0) return fail(PCS_EINVAL, "n_iter must be >= 0 (got %d)", n_iter);
+    if (field == chi_out) return fail(PCS_EINVAL, "chi_out must not alias field");
+    return PCS_OK;
+}
+
+pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
+                        double tau, double sigma, int n_iter, float* chi_out) {
+    if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out))
+        return fail(PCS_EINVAL, "device buffers must be 16-byte aligned");
+    pcs::PDParams prm;
+    prm.field = field;
+    prm.mask = mask;
+    prm.chi = chi_out;
+    prm.chibar = ctx->chibar;
+    prm.p = ctx->p;
+    prm.qx = ctx->qx;
+    prm.qy = ctx->qy;
+    prm.dtab = ctx->dtab;
+    prm.ddtab = ctx->ddtab;
+    prm.twid = ctx->twid;
+    prm.S = S;
+    prm.n_iter = n_iter;
+    prm.sigma = (float)sigma;
+    prm.tau = (float)tau;
+    prm.inv_den = (float)(1.0 / (1.0 + sigma / lambda));
+    int ncl = ctx->max_clusters;
+    if (ctx->opt.max_clusters > 0 && ctx->opt.max_clusters < ncl) ncl = ctx->opt.max_clusters;
+    if (ncl > S) ncl = S;
+    if (ncl < 1) ncl = 1;
+    PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    PCS_CUDA(ctx->entry->launch(prm, ncl, ctx->stream), "launch of the primal-dual kernel");
+    ctx->last_iters = n_iter;
+    return PCS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ diagnostics and step size
+
+namespace {
+
+pcs_status ensure_aux(pcs_ctx* c) {
+    if (c->partials) return PCS_OK;
+    const size_t n = slice_elems(c) * (size_t)c->max_slices;
+    PCS_CUDA(cudaMalloc(&c->partials, (size_t)c->max_slices * c->entry->C * pcs::kReportSums * sizeof(double)),
+             "cudaMalloc partials");
+    PCS_CUDA(cudaMalloc(&c->Ldev, (size_t)c->max_slices * sizeof(double)), "cudaMalloc L");
+    PCS_CUDA(cudaMalloc(&c->xa, n * sizeof(float)), "cudaMalloc power-iteration buffer");
+    PCS_CUDA(cudaMalloc(&c->xb, n * sizeof(float)), "cudaMalloc power-iteration buffer");
+    return PCS_OK;
+}
+
+pcs::AuxParams aux_params(pcs_ctx* c, int S) {
+    pcs::AuxParams a{};
+    a.dtab = c->dtab;
+    a.ddtab = c->ddtab;
+    a.twid = c->twid;
+    a.partials = c->partials;
+    a.Lout = c->Ldev;
+    a.xa = c->xa;
+    a.xb = c->xb;
+    a.p = c->p;
+    a.qx = c->qx;
+    a.qy = c->qy;
+    a.S = S;
+    return a;
+}
+
+int aux_clusters(pcs_ctx* c, int S) {
+    int ncl = c->max_clusters_aux;
+    if (ncl > S) ncl = S;
+    return ncl < 1 ? 1 : ncl;
+}
+
+}  // namespace
+
+namespace pcs {
+
+// Objective, Fenchel-Young gap, stationarity and residual of every slice at
+// (chi, p, q) where p, q are the context's dual state of the last solve.
+pcs_status ctx_report(pcs_ctx* c, const float* field, const unsigned char* mask, int S, double lambda,
+                      const float* chi, pcs_slice_report* rep) {
+    pcs_status st = ensure_aux(c);
+    if (st != PCS_OK) return st;
+    AuxParams a = aux_params(c, S);
+    a.field = field;
+    a.mask = mask;
+    a.chi = chi;
+    a.lam = (float)lambda;
+    PCS_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    PCS_CUDA(c->entry->launch_report(a, aux_clusters(c, S), c->stream), "launch of the report kernel");
+    const int C = c->entry->C;
+    std::vector<double> h((size_t)S * C * kReportSums);
+    PCS_CUDA(cudaMemcpyAsync(h.data(), c->partials, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+             "D2H partials");
+    PCS_CUDA(cudaStreamSynchronize(c->stream), "stream sync");
+    for (int s = 0; s < S; ++s) {
+        double v[kReportSums] = {0, 0, 0, 0, 0};
+        for (int q = 0; q < C; ++q)
+            for (int t = 0; t < kReportSums; ++t) v[t] += h[((size_t)s * C + q) * kReportSums + t];
+        rep[s].objective = 0.5 * lambda * v[0] + v[1];
+        rep[s].gap = v[2] / (2.0 * lambda) + v[3];
+        rep[s].stationarity = std::sqrt(v[4]);
+        rep[s].data_residual = std::sqrt(v[0]);
+        rep[s].iters = c->last_iters;
+        rep[s].pad = 0;
+    }
+    return PCS_OK;
+}
+
+pcs_status ctx_opnorm(pcs_ctx* c, const unsigned char* mask, int S, int power_iters, double* L_out) {
+    pcs_status st = ensure_aux(c);
+    if (st != PCS_OK) return st;
+    AuxParams a = aux_params(c, S);
+    a.mask = mask;
+    a.iters = power_iters;
+    PCS_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+    PCS_CUDA(c->entry->launch_opnorm(a, aux_clusters(c, S), c->stream), "launch of the power-iteration kernel");
+    PCS_CUDA(cudaMemcpyAsync(L_out, c->Ldev, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+             "D2H L");
+    PCS_CUDA(cudaStreamSynchronize(c->stream), "stream sync");
+    return PCS_OK;
+}
+
+}  // namespace pcs
+
+extern "C" {
+
+pcs_status pcs_options_default(pcs_options* opt) {
+    if (!opt) return fail(PCS_EINVAL, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    return PCS_OK;
+}
+
+int pcs_supported_size(int H, int W) { return find_entry(H, W, 0) != nullptr ? 1 : 0; }
+
+pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_options* opt, void* cuda_stream) {
+    if (!out) return fail(PCS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (max_slices < 1) return fail(PCS_EINVAL, "max_slices must be >= 1 (got %d)", max_slices);
+    pcs_options o;
+    pcs_options_default(&o);
+    if (opt) o = *opt;
+    if (o.b0_axis != 0 && o.b0_axis != 1) return fail(PCS_EINVAL, "b0_axis must be 0 or 1");
+    const pcs::KernelEntry* entry = find_entry(H, W, o.cluster_size);
+    if (!entry)
+        return fail(PCS_EUNSUPPORTED, "no kernel for %d x %d slices with cluster_size %d", H, W, o.cluster_size);
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) return fail(PCS_ECUDA, "no CUDA device (%s)", cudaGetErrorString(e));
+
+    pcs_ctx* c = new pcs_ctx();
+    c->H = H;
+    c->W = W;
+    c->max_slices = max_slices;
+    c->opt = o;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->entry = entry;
+    auto bail = [&](pcs_status st) {
+        free_ctx(c);
+        return st;
+    };
+    if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+    if ((e = entry->prepare(&c->max_clusters, &c->max_clusters_aux)) != cudaSuccess) return bail(cuda_fail(e, "kernel attributes"));
+    if (c->max_clusters < 1)
+        return bail(fail(PCS_ECUDA, "kernel %dx%d/C=%d cannot be made resident", H, W, entry->C));
+
+    std::vector<float> dtab, ddtab;
+    std::vector<float2> tw;
+    pcs::build_dipole_tables(H, W, o.b0_axis, dtab, ddtab);
+    pcs::build_twiddles(H > W ? H : W, tw);
+    const size_t n = slice_elems(c) * (size_t)max_slices;
+    struct {
+        void** ptr;
+        size_t bytes;
+    } allocs[] = {
+        {(void**)&c->dtab, dtab.size() * sizeof(float)},  {(void**)&c->ddtab, ddtab.size() * sizeof(float)},
+        {(void**)&c->twid, tw.size() * sizeof(float2)},   {(void**)&c->chibar, n * sizeof(float)},
+        {(void**)&c->p, n * sizeof(float)},               {(void**)&c->qx, n * sizeof(float)},
+        {(void**)&c->qy, n * sizeof(float)},
+    };
+    for (auto& a : allocs)
+        if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    if ((e = cudaMemcpy(c->dtab, dtab.data(), dtab.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->ddtab, ddtab.data(), ddtab.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->twid, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(e, "table upload"));
+    *out = c;
+    return PCS_OK;
+}
+
+pcs_status pcs_set_stream(pcs_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return PCS_OK;
+}
+
+pcs_status pcs_solve_slices(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
+                            double tau, double sigma, int n_iter, float* chi_out, pcs_slice_report* rep) {
+    pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
+    if (st != PCS_OK || S == 0) return st;
+    std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
+    st = launch_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
+    if (st != PCS_OK || !rep) return st;
+    return pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, rep);
+}
+
+pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const unsigned char* mask_host, int S,
+                                 double lambda, double tau, double sigma, int n_iter, float* chi_out_host,
+                                 pcs_slice_report* rep) {
+    pcs_status st = validate_solve(ctx, field_host, mask_host, S, lambda, tau, sigma, n_iter, chi_out_host);
+    if (st != PCS_OK || S == 0) return st;
+    std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
+    PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const size_t n = slice_elems(ctx) * (size_t)ctx->max_slices;
+    if (!ctx->st_field) {
+        PCS_CUDA(cudaMalloc(&ctx->st_field, n * sizeof(float)), "cudaMalloc staging");
+        PCS_CUDA(cudaMalloc(&ctx->st_mask, n), "cudaMalloc staging");
+        PCS_CUDA(cudaMalloc(&ctx->st_chi, n * sizeof(float)), "cudaMalloc staging");
+    }
+    const size_t m = slice_elems(ctx) * (size_t)S;
+    PCS_CUDA(cudaMemcpyAsync(ctx->st_field, field_host, m * sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
+             "H2D field");
+    PCS_CUDA(cudaMemcpyAsync(ctx->st_mask, mask_host, m, cudaMemcpyHostToDevice, ctx->stream), "H2D mask");
+    st = launch_solve(ctx, ctx->st_field, ctx->st_mask, S, lambda, tau, sigma, n_iter, ctx->st_chi);
+    if (st != PCS_OK) return st;
+    PCS_CUDA(cudaMemcpyAsync(chi_out_host, ctx->st_chi, m * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
+             "D2H chi");
+    PCS_CUDA(cudaStreamSynchronize(ctx->stream), "stream sync");
+    if (rep) return pcs::ctx_report(ctx, ctx->st_field, ctx->st_mask, S, lambda, ctx->st_chi, rep);
+    return PCS_OK;
+}
+
+pcs_status pcs_report(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
+                      const float* chi, pcs_slice_report* rep) {
+    if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
+    if (S < 0 || S > ctx->max_slices) return fail(PCS_EINVAL, "S=%d outside [0, max_slices]", S);
+    if (S == 0) return PCS_OK;
+    if (!field || !mask || !chi || !rep) return fail(PCS_EINVAL, "NULL argument");
+    if (!(lambda > 0.0)) return fail(PCS_EINVAL, "lambda must be > 0");
+    return pcs::ctx_report(ctx, field, mask, S, lambda, chi, rep);
+}
+
+pcs_status pcs_opnorm(pcs_ctx* ctx, const unsigned char* mask, int S, int power_iters, double* L_out) {
+    if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
+    if (S < 0 || S > ctx->max_slices) return fail(PCS_EINVAL, "S=%d outside [0, max_slices]", S);
+    if (S == 0) return PCS_OK;
+    if (!mask || !L_out) return fail(PCS_EINVAL, "NULL argument");
+    if (power_iters < 1) return fail(PCS_EINVAL, "power_iters must be >= 1");
+    return pcs::ctx_opnorm(ctx, mask, S, power_iters, L_out);
+}
+
+void pcs_destroy(pcs_ctx* ctx) { free_ctx(ctx); }
+
+const char* pcs_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

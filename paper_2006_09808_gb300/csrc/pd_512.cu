@@ -1,0 +1,12 @@
+// Fused primal-dual kernel instances for 512 x 512 slices.
+#include "pd_launch.cuh"
+
+namespace pcs {
+static const KernelEntry k_entries[] = {
+    make_entry<Geo<512, 512, 8, 1>>(),
+};
+const KernelEntry* entries_512(int* n) {
+    *n = (int)(sizeof(k_entries) / sizeof(k_entries[0]));
+    return k_entries;
+}
+}  // namespace pcs

@@ -1,0 +1,405 @@
+// pd_cluster.cuh -- the fused primal-dual iteration: one thread-block cluster
+// per slice, the slice's spectrum distributed over the cluster's shared
+// memory, every step of the Sec. II.A pseudocode fused around the FFT passes.
+//
+// Data flow of one iteration for slice s (C CTAs; CTA c owns rows
+// [c R, (c+1) R) of the slice and spectrum columns [c MC, (c+1) MC)):
+//
+//   column pass   (own spectrum columns)  F_y, x D(k)/(HW), F_y^-1         -> u-spectrum
+//   cluster barrier
+//   row phase B   (own rows)   gather row from all CTAs (DSMEM), real F_x^-1 -> u = D chibar
+//                              p <- (p + sigma W (u - f)) / (1 + sigma/lambda)     dual data prox
+//                              q <- clamp(q + sigma M G chibar)                   dual TV prox
+//                              real F_x of W p, scatter row to all CTAs (DSMEM)
+//   cluster barrier
+//   column pass                                                            -> v-spectrum
+//   cluster barrier
+//   row phase A   (own rows)   gather, real F_x^-1 -> v = D W p
+//                              chi+ = chi - tau v - tau G^T M q                 primal step
+//                              chibar = 2 chi+ - chi                             over-relaxation
+//                              real F_x of chibar, scatter (not on the last iteration)
+//   cluster barrier
+//
+// The real row transforms use the half-length complex FFT of
+// z[n] = x[2n] + i x[2n+1]; the packed row spectrum stores X[0] + i X[W/2] in
+// column 0.  The column pass handles that packed column by pairing ky with -ky
+// (both halves are spectra of real columns):
+//   Y[ky] = Dm[ky] C[ky] + Dd[ky] conj(C[-ky]),  Dm,Dd = (D(ky,0) +- D(ky,W/2))/2.
+// All normalisation (1/(H W)) is folded into the D table.
+//
+// State (chi = the caller's chi_out, chibar, p, qx, qy) stays in global
+// memory (L2/HBM) and is touched once per phase; the FFT intermediates never
+// leave the chip.  The kernel is persistent: a cluster loops over slices
+// s = cluster_id, cluster_id + n_clusters, ...  There is no grid-wide
+// synchronisation and no spin-wait: the only waits are hardware cluster
+// barriers.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "fft_core.cuh"
+
+namespace pcs {
+
+namespace cg = cooperative_groups;
+
+struct PDParams {
+    const float* field;         // [S][H][W]
+    const unsigned char* mask;  // [S][H][W]
+    float* chi;                 // [S][H][W]  (caller's chi_out)
+    float* chibar;              // [S][H][W]  scratch
+    float* p;                   // [S][H][W]  scratch
+    float* qx;                  // [S][H][W]  scratch
+    float* qy;                  // [S][H][W]  scratch
+    const float* dtab;          // [W/2][H]: D(ky,kx)/(HW), column kx=0 holds Dm
+    const float* ddtab;         // [H]: Dd for the packed column
+    const float2* twid;         // [NTW]: exp(-2 pi i m / NTW)
+    int S;
+    int n_iter;
+    float sigma;
+    float tau;
+    float inv_den;  // 1 / (1 + sigma / lambda)
+};
+
+constexpr int ceil_to_mod16(int v, int want) {  // smallest x >= v with x % 16 == want % 16
+    return v + ((want % 16) - (v % 16) + 16) % 16;
+}
+
+template <int H_, int W_, int C_, int MINB_ = 1, int NT_ = 256>
+struct Geo {
+    static constexpr int H = H_, W = W_, C = C_, NT = NT_, MINB = MINB_;
+    static constexpr int M = W / 2;    // complex row length (packed half spectrum)
+    static constexpr int R = H / C;    // rows per CTA
+    static constexpr int MC = M / C;   // spectrum columns per CTA
+    static constexpr int NTW = (H > W) ? H : W;
+    // row transforms (length M)
+    static constexpr int ER = (M >= 128) ? 16 : 8;
+    static constexpr int TR = M / ER;
+    // column transforms (length H)
+    static constexpr int EC = (H >= 128) ? 16 : 8;
+    static constexpr int TC = H / EC;
+    static constexpr int NW = NT / 32;
+    static constexpr int RPP = NW * (32 / TR);  // rows in flight per CTA
+    static constexpr int CPP = NW * (32 / TC);  // columns in flight per CTA
+    // shared-memory layout (float2 units)
+    static constexpr int HP = H + H / 16 + 1;                        // column stride (odd)
+    static constexpr int MP = ceil_to_mod16(M + M / 16, TR % 16);    // row-scratch stride
+    static constexpr int SM_TBUF = MC * HP;
+    static constexpr int SM_ROWS = RPP * MP;
+    static constexpr int SM_TW = NTW;
+    static constexpr size_t SMEM_BYTES = sizeof(float2) * (SM_TBUF + SM_ROWS + SM_TW);
+
+    static_assert(TR <= 32 && TC <= 32, "group fits a warp");
+    static_assert(R % RPP == 0, "row passes");
+    static_assert(MC % CPP == 0, "column passes");
+    static_assert(MC % TR == 0, "gather/scatter owner is compile-time per element");
+    static_assert(W % 4 == 0 && H % 16 == 0, "shape");
+};
+
+template <int T>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+    if constexpr (T == 32) {
+        return 0xffffffffu;
+    } else {
+        return ((1u << T) - 1u) << ((lane / T) * T);
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void cluster_barrier() {
+    if constexpr (C == 1) {
+        __syncthreads();
+    } else {
+        cg::this_cluster().sync();
+    }
+}
+
+template <class G>
+struct Ctx {
+    float2* tbuf;     // own spectrum columns, [MC][HP]
+    float2* rows;     // row scratch, [RPP][MP]
+    float2* tw;       // twiddles [NTW]
+    float2* tb[G::C]; // spectrum columns of every CTA of the cluster (DSMEM)
+    int crank;
+};
+
+// ------------------------------------------------------------------ column pass
+// Forward column FFT, multiply by D/(HW), inverse column FFT, in place on the
+// CTA's own spectrum columns.
+template <class G>
+__device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __restrict__ dtab,
+                                            const float* __restrict__ ddtab) {
+    constexpr int H = G::H, TC = G::TC, EC = G::EC, NTW = G::NTW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % TC;
+    const int grp = warp * (32 / TC) + lane / TC;
+    const unsigned gm = group_mask<TC>(lane);
+#pragma unroll 1
+    for (int pass = 0; pass < G::MC / G::CPP; ++pass) {
+        const int cl = pass * G::CPP + grp;
+        const int kx = cx.crank * G::MC + cl;
+        float2* col = cx.tbuf + cl * G::HP;
+        float2 x[EC];
+#pragma unroll
+        for (int e = 0; e < EC; ++e) x[e] = col[P(g + TC * e)];
+        fft<H, TC, false, NTW / H>(x, col, cx.tw, g, gm);
+        if (kx != 0) {
+            const float* d = dtab + (size_t)kx * H;
+#pragma unroll
+            for (int e = 0; e < EC; ++e) x[e] = cscale(x[e], __ldg(d + g + TC * e));
+        } else {
+            // packed DC / Nyquist column: pair ky with -ky
+#pragma unroll
+            for (int e = 0; e < EC; ++e) col[P(g + TC * e)] = x[e];
+            __syncwarp(gm);
+#pragma unroll
+            for (int e = 0; e < EC; ++e) {
+                const int ky = g + TC * e;
+                const float2 ym = col[P((H - ky) & (H - 1))];
+                const float dm = __ldg(dtab + ky), dd = __ldg(ddtab + ky);
+                x[e] = make_float2(fmaf(dm, x[e].x, dd * ym.x), fmaf(dm, x[e].y, -dd * ym.y));
+            }
+        }
+        fft<H, TC, true, NTW / H>(x, col, cx.tw, g, gm);
+#pragma unroll
+        for (int e = 0; e < EC; ++e) col[P(g + TC * e)] = x[e];
+        __syncwarp(gm);
+    }
+}
+
+// ------------------------------------------------------------------ row transforms
+// Gather packed spectrum row i from the cluster and apply the inverse real
+// row transform.  Result: x[e] = W * (y[2n], y[2n+1]) for n = g + TR*e, where
+// y is the real row (the D table carries 1/(HW), so x is the true D-product).
+template <class G>
+__device__ __forceinline__ void row_inverse(const Ctx<G>& cx, float2* rs, int i, int g, unsigned gm,
+                                            float2 (&x)[G::ER]) {
+    constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
+#pragma unroll
+    for (int e = 0; e < ER; ++e) {
+        const int k = g + TR * e;
+        const int q = (TR * e) / MC;  // compile-time after unrolling
+        const int cl = k - q * MC;
+        rs[P(k)] = cx.tb[q][cl * G::HP + P(i)];
+    }
+    __syncwarp(gm);
+#pragma unroll
+    for (int e = 0; e < ER; ++e) {
+        const int k = g + TR * e;
+        const float2 X = rs[P(k)];
+        if (k == 0) {
+            // X[0] = Re, X[M] = Im of the packed entry
+            x[e] = make_float2(X.x + X.y, X.x - X.y);
+        } else {
+            const float2 Xm = rs[P(M - k)];
+            const float2 ec = make_float2(X.x + Xm.x, X.y - Xm.y);   // X + conj(Xm)
+            const float2 od0 = make_float2(X.x - Xm.x, X.y + Xm.y);  // X - conj(Xm)
+            const float2 w = cx.tw[k * (NTW / W)];                    // exp(-2 pi i k / W)
+            const float2 od = cmul(od0, conjf2(w));
+            x[e] = make_float2(ec.x - od.y, ec.y + od.x);  // ec + i od
+        }
+    }
+    fft<M, TR, true, NTW / M>(x, rs, cx.tw, g, gm);
+}
+
+// Forward real row transform of z[e] = (x[2n], x[2n+1]), n = g + TR*e, and
+// scatter of the packed spectrum row i to the owners of its columns.
+template <class G>
+__device__ __forceinline__ void row_forward(const Ctx<G>& cx, float2* rs, int i, int g, unsigned gm,
+                                            float2 (&z)[G::ER]) {
+    constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
+    fft<M, TR, false, NTW / M>(z, rs, cx.tw, g, gm);
+#pragma unroll
+    for (int e = 0; e < ER; ++e) rs[P(g + TR * e)] = z[e];
+    __syncwarp(gm);
+#pragma unroll
+    for (int e = 0; e < ER; ++e) {
+        const int k = g + TR * e;
+        const float2 A = z[e];
+        float2 out;
+        if (k == 0) {
+            out = make_float2(A.x + A.y, A.x - A.y);  // X[0] + i X[M]
+        } else {
+            const float2 Zm = rs[P(M - k)];
+            // E = (A + conj(Zm))/2, O = -i (A - conj(Zm))/2, X = E + w^k O
+            const float2 E = make_float2(0.5f * (A.x + Zm.x), 0.5f * (A.y - Zm.y));
+            const float2 dlt = make_float2(A.x - Zm.x, A.y + Zm.y);
+            const float2 O = make_float2(0.5f * dlt.y, -0.5f * dlt.x);
+            const float2 w = cx.tw[k * (NTW / W)];
+            out = cadd(E, cmul(w, O));
+        }
+        const int q = (TR * e) / MC;
+        const int cl = k - q * MC;
+        cx.tb[q][cl * G::HP + P(i)] = out;
+    }
+    __syncwarp(gm);
+}
+
+// ------------------------------------------------------------------ row phases
+
+// Phase B: u = D chibar -> dual proxes -> forward transform of W p.
+template <class G>
+__device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm, size_t base) {
+    constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % TR;
+    const int grp = warp * (32 / TR) + lane / TR;
+    const unsigned gm = group_mask<TR>(lane);
+    float2* rs = cx.rows + grp * G::MP;
+    const float sigma = prm.sigma, inv_den = prm.inv_den;
+#pragma unroll 1
+    for (int pass = 0; pass < G::R / G::RPP; ++pass) {
+        const int i = cx.crank * G::R + pass * G::RPP + grp;
+        float2 x[ER];
+        row_inverse<G>(cx, rs, i, g, gm, x);
+        const size_t rowoff = base + (size_t)i * W;
+        const bool has_down = (i + 1 < H);
+#pragma unroll
+        for (int e = 0; e < ER; ++e) {
+            const int n = g + TR * e;
+            const int j0 = 2 * n;
+            const size_t o = rowoff + j0;
+            const float2 u = x[e];
+            const float2 f = __ldg(reinterpret_cast<const float2*>(prm.field + o));
+            const uchar2 mk = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o));
+            const float m0 = (float)mk.x, m1 = (float)mk.y;
+            float2 p = __ldcg(reinterpret_cast<const float2*>(prm.p + o));
+            // dual data prox (W = mask, W dB computed on the fly)
+            p.x = (p.x + sigma * (m0 * (u.x - f.x))) * inv_den;
+            p.y = (p.y + sigma * (m1 * (u.y - f.y))) * inv_den;
+            __stcg(reinterpret_cast<float2*>(prm.p + o), p);
+            // dual TV prox (forward differences of chibar, Neumann boundary)
+            const float2 cb = __ldcg(reinterpret_cast<const float2*>(prm.chibar + o));
+            const float cr = (j0 + 2 < W) ? __ldcg(prm.chibar + o + 2) : cb.y;
+            float2 cd = cb;
+            if (has_down) cd = __ldcg(reinterpret_cast<const float2*>(prm.chibar + o + W));
+            float2 qx = __ldcg(reinterpret_cast<const float2*>(prm.qx + o));
+            float2 qy = __ldcg(reinterpret_cast<const float2*>(prm.qy + o));
+            qx.x = fminf(1.f, fmaxf(-1.f, qx.x + sigma * m0 * (cb.y - cb.x)));
+            qx.y = fminf(1.f, fmaxf(-1.f, qx.y + sigma * m1 * (cr - cb.y)));
+            qy.x = fminf(1.f, fmaxf(-1.f, qy.x + sigma * m0 * (cd.x - cb.x)));
+            qy.y = fminf(1.f, fmaxf(-1.f, qy.y + sigma * m1 * (cd.y - cb.y)));
+            __stcg(reinterpret_cast<float2*>(prm.qx + o), qx);
+            __stcg(reinterpret_cast<float2*>(prm.qy + o), qy);
+            x[e] = make_float2(m0 * p.x, m1 * p.y);  // W p: input of the adjoint transform
+        }
+        row_forward<G>(cx, rs, i, g, gm, x);
+    }
+}
+
+// Phase A: v = D W p -> primal step -> over-relaxation -> forward transform of chibar.
+template <class G>
+__device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParams& prm, size_t base,
+                                             bool last) {
+    constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % TR;
+    const int grp = warp * (32 / TR) + lane / TR;
+    const unsigned gm = group_mask<TR>(lane);
+    float2* rs = cx.rows + grp * G::MP;
+    const float tau = prm.tau;
+#pragma unroll 1
+    for (int pass = 0; pass < G::R / G::RPP; ++pass) {
+        const int i = cx.crank * G::R + pass * G::RPP + grp;
+        float2 x[ER];
+        row_inverse<G>(cx, rs, i, g, gm, x);
+        const size_t rowoff = base + (size_t)i * W;
+        const bool has_up = (i > 0), has_down = (i + 1 < H);
+#pragma unroll
+        for (int e = 0; e < ER; ++e) {
+            const int n = g + TR * e;
+            const int j0 = 2 * n;
+            const size_t o = rowoff + j0;
+            const float2 v = x[e];
+            const uchar2 mk = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o));
+            const float m0 = (float)mk.x, m1 = (float)mk.y;
+            const float2 qx = __ldcg(reinterpret_cast<const float2*>(prm.qx + o));
+            const float2 qy = __ldcg(reinterpret_cast<const float2*>(prm.qy + o));
+            // a = M qx, b = M qy;  G^T(a,b)[j] = a[j-1][j>0] - a[j][j<W-1] + b[i-1][i>0] - b[i][i<H-1]
+            const float a0 = m0 * qx.x, a1 = m1 * qx.y;
+            float al = 0.f;
+            if (j0 > 0) al = (float)__ldg(prm.mask + o - 1) * __ldcg(prm.qx + o - 1);
+            const float a1r = (j0 + 2 < W) ? a1 : 0.f;  // a[j1] counts only if j1 < W-1
+            float bu0 = 0.f, bu1 = 0.f;
+            if (has_up) {
+                const uchar2 mu = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o - W));
+                const float2 qu = __ldcg(reinterpret_cast<const float2*>(prm.qy + o - W));
+                bu0 = (float)mu.x * qu.x;
+                bu1 = (float)mu.y * qu.y;
+            }
+            const float b0 = has_down ? m0 * qy.x : 0.f;
+            const float b1 = has_down ? m1 * qy.y : 0.f;
+            const float d0 = (al - a0) + (bu0 - b0);
+            const float d1 = (a0 - a1r) + (bu1 - b1);
+            const float2 chi = __ldcg(reinterpret_cast<const float2*>(prm.chi + o));
+            float2 cn;
+            cn.x = chi.x - tau * v.x - tau * d0;
+            cn.y = chi.y - tau * v.y - tau * d1;
+            __stcg(reinterpret_cast<float2*>(prm.chi + o), cn);
+            const float2 cb = make_float2(2.f * cn.x - chi.x, 2.f * cn.y - chi.y);
+            if (!last) __stcg(reinterpret_cast<float2*>(prm.chibar + o), cb);
+            x[e] = cb;
+        }
+        if (!last) row_forward<G>(cx, rs, i, g, gm, x);
+    }
+}
+
+// ------------------------------------------------------------------ kernel
+
+template <class G>
+__global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParams prm) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Ctx<G> cx;
+    cx.tbuf = reinterpret_cast<float2*>(smem_raw);
+    cx.rows = cx.tbuf + G::SM_TBUF;
+    cx.tw = cx.rows + G::SM_ROWS;
+    if constexpr (G::C == 1) {
+        cx.crank = 0;
+        cx.tb[0] = cx.tbuf;
+    } else {
+        cg::cluster_group cluster = cg::this_cluster();
+        cx.crank = (int)cluster.block_rank();
+#pragma unroll
+        for (int q = 0; q < G::C; ++q) cx.tb[q] = cluster.map_shared_rank(cx.tbuf, q);
+    }
+    for (int t = threadIdx.x; t < G::NTW; t += G::NT) cx.tw[t] = prm.twid[t];
+
+    const int cid = blockIdx.x / G::C;
+    const int ncl = gridDim.x / G::C;
+    constexpr size_t SLICE = (size_t)G::H * G::W;
+    constexpr int OWN = G::R * G::W;  // floats of own rows
+
+#pragma unroll 1
+    for (int s = cid; s < prm.S; s += ncl) {
+        const size_t base = (size_t)s * SLICE;
+        // zero start (pseudocode steps 2-3): chi, chibar, p, q of own rows, own spectrum
+        {
+            const size_t o = base + (size_t)cx.crank * OWN;
+            float4* ptrs[5] = {reinterpret_cast<float4*>(prm.chi + o), reinterpret_cast<float4*>(prm.chibar + o),
+                               reinterpret_cast<float4*>(prm.p + o), reinterpret_cast<float4*>(prm.qx + o),
+                               reinterpret_cast<float4*>(prm.qy + o)};
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < 5; ++a)
+                for (int t = threadIdx.x; t < OWN / 4; t += G::NT) __stcg(ptrs[a] + t, z4);
+            for (int t = threadIdx.x; t < G::SM_TBUF; t += G::NT) cx.tbuf[t] = make_float2(0.f, 0.f);
+        }
+        cluster_barrier<G::C>();
+#pragma unroll 1
+        for (int n = 0; n < prm.n_iter; ++n) {
+            if (n > 0) {
+                column_pass<G>(cx, prm.dtab, prm.ddtab);  // u-spectrum = D F chibar_n
+                cluster_barrier<G::C>();
+            }
+            phase_dual<G>(cx, prm, base);
+            cluster_barrier<G::C>();
+            column_pass<G>(cx, prm.dtab, prm.ddtab);  // v-spectrum = D F (W p_{n+1})
+            cluster_barrier<G::C>();
+            phase_primal<G>(cx, prm, base, n + 1 == prm.n_iter);
+            cluster_barrier<G::C>();
+        }
+    }
+}
+
+}  // namespace pcs

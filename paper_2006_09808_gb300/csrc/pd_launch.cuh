@@ -1,0 +1,106 @@
+// pd_launch.cuh -- launch glue shared by the per-size translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pd_aux.cuh"
+#include "pd_cluster.cuh"
+
+namespace pcs {
+
+// One compiled (H, W, cluster size) variant: the iteration kernel and its
+// diagnostics / step-size companions.
+struct KernelEntry {
+    int H, W, C;
+    size_t smem;
+    int threads;
+    // Sets function attributes; returns how many clusters of the iteration
+    // kernel and of the auxiliary kernels can be resident.
+    cudaError_t (*prepare)(int* max_clusters, int* max_clusters_aux);
+    cudaError_t (*launch)(const PDParams& prm, int n_clusters, cudaStream_t stream);
+    cudaError_t (*launch_report)(const AuxParams& prm, int n_clusters, cudaStream_t stream);
+    cudaError_t (*launch_opnorm)(const AuxParams& prm, int n_clusters, cudaStream_t stream);
+};
+
+template <class G>
+constexpr size_t aux_smem() {
+    return G::SMEM_BYTES + 64 * sizeof(double);
+}
+
+template <class G, class P>
+cudaError_t launch_cluster(void (*kern)(P), const P& prm, size_t smem, int n_clusters, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_clusters * G::C, 1, 1);
+    cfg.blockDim = dim3(G::NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, prm);
+}
+
+template <class G, class P>
+cudaError_t prepare_cluster(void (*kern)(P), size_t smem, int* max_clusters) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (G::C > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G::C, 1, 1);
+    cfg.blockDim = dim3(G::NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(max_clusters, kern, &cfg);
+}
+
+template <class G>
+cudaError_t launch_pd(const PDParams& prm, int n_clusters, cudaStream_t stream) {
+    return launch_cluster<G>(pd_cluster_kernel<G>, prm, G::SMEM_BYTES, n_clusters, stream);
+}
+template <class G>
+cudaError_t launch_report(const AuxParams& prm, int n_clusters, cudaStream_t stream) {
+    return launch_cluster<G>(aux_report_kernel<G>, prm, aux_smem<G>(), n_clusters, stream);
+}
+template <class G>
+cudaError_t launch_opnorm(const AuxParams& prm, int n_clusters, cudaStream_t stream) {
+    return launch_cluster<G>(aux_opnorm_kernel<G>, prm, aux_smem<G>(), n_clusters, stream);
+}
+
+template <class G>
+cudaError_t prepare_all(int* max_clusters, int* max_clusters_aux) {
+    cudaError_t e = prepare_cluster<G>(pd_cluster_kernel<G>, G::SMEM_BYTES, max_clusters);
+    if (e != cudaSuccess) return e;
+    int a = 0, b = 0;
+    if ((e = prepare_cluster<G>(aux_report_kernel<G>, aux_smem<G>(), &a)) != cudaSuccess) return e;
+    if ((e = prepare_cluster<G>(aux_opnorm_kernel<G>, aux_smem<G>(), &b)) != cudaSuccess) return e;
+    *max_clusters_aux = a < b ? a : b;
+    return cudaSuccess;
+}
+
+template <class G>
+constexpr KernelEntry make_entry() {
+    return KernelEntry{G::H,           G::W,           G::C,
+                       G::SMEM_BYTES,  G::NT,          &prepare_all<G>,
+                       &launch_pd<G>,  &launch_report<G>, &launch_opnorm<G>};
+}
+
+// Per-size translation units define these (pd_<size>.cu).
+const KernelEntry* entries_64(int* n);
+const KernelEntry* entries_128(int* n);
+const KernelEntry* entries_256(int* n);
+const KernelEntry* entries_512(int* n);
+
+}  // namespace pcs

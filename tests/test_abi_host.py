@@ -1,0 +1,89 @@
+"""The C ABI without a GPU: the library builds, loads, exports every declared
+symbol, and rejects bad arguments with status codes (no compute calls)."""
+
+import ctypes
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import paper_2006_09808_gb300 as pcs
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists(pcs.LIB_PATH),
+                                reason="needs nvcc or a built libpcs.so")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2006_09808_gb300 import build
+
+    build.build()
+    return pcs.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = pcs.declared_functions()
+    for n in ("pcs_create", "pcs_solve_slices", "pcs_destroy", "pcs_opnorm", "pcs_report",
+              "pcs_solve_slices_host", "pcs_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", pcs.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in pcs.declared_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_only_the_c_abi_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", pcs.LIB_PATH], capture_output=True, text=True).stdout
+    ours = {line.split()[-1] for line in out.splitlines() if " T " in line and "pcs" in line}
+    assert ours == set(pcs.declared_functions())
+
+
+def test_host_side_argument_checks(lib):
+    opt = pcs.pcs_options()
+    assert lib.pcs_options_default(ctypes.byref(opt)) == pcs.PCS_OK
+    assert (opt.b0_axis, opt.cluster_size, opt.max_clusters) == (0, 0, 0)
+    assert lib.pcs_options_default(None) == pcs.PCS_EINVAL
+    assert lib.pcs_supported_size(256, 256) == 1
+    assert lib.pcs_supported_size(64, 64) == 1
+    assert lib.pcs_supported_size(100, 100) == 0
+    h = ctypes.c_void_p()
+    assert lib.pcs_create(None, 64, 64, 1, None, None) == pcs.PCS_EINVAL
+    assert lib.pcs_create(ctypes.byref(h), 64, 64, 0, None, None) == pcs.PCS_EINVAL
+    assert h.value is None
+    assert lib.pcs_create(ctypes.byref(h), 100, 100, 4, None, None) == pcs.PCS_EUNSUPPORTED
+    assert "100 x 100" in pcs.last_error()
+    bad = pcs.pcs_options()
+    bad.b0_axis = 3
+    assert lib.pcs_create(ctypes.byref(h), 64, 64, 4, ctypes.byref(bad), None) == pcs.PCS_EINVAL
+    assert lib.pcs_solve_slices(None, None, None, 1, 1.0, 1.0, 1.0, 1, None, None) == pcs.PCS_EINVAL
+    assert lib.pcs_opnorm(None, None, 1, 10, None) == pcs.PCS_EINVAL
+    lib.pcs_destroy(None)  # NULL-safe
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = lib.pcs_create(ctypes.byref(h), 64, 64, 1, None, None)
+    assert st == pcs.PCS_ECUDA and h.value is None
+    assert pcs.last_error() != ""
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    import importlib
+
+    mod = importlib.reload(pcs)
+    saved = mod._lib
+    try:
+        mod._lib = None
+        with pytest.raises(RuntimeError, match="libpcs.so not found"):
+            mod.load_library(str(tmp_path / "missing.so"))
+    finally:
+        mod._lib = saved
