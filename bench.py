@@ -1,0 +1,350 @@
+"""Benchmark: primal-dual voxel-iterations/s on the 256 x 256 x 64-slice volume.
+
+One step = one complete solve of the hot path on one batch: zero start and
+500 fused primal-dual iterations (forward dipole convolution, dual data and
+TV proxes, adjoint convolution, primal step, over-relaxation) for all 64
+slices of the synthetic 256 x 256 volume (six seeds/needles in smooth tissue,
+elliptical mask, lambda = 5e-4), inputs resident in HBM.  The L2 cache is
+flushed (a 256 MiB device write) between timed steps; within a step the
+iteration's working set stays wherever the hardware keeps it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+
+Multi-GPU (torchrun, one rank per GPU): slices are independent, so every rank
+solves its own volume with no data-path collective (weak scaling); the
+barrier and the max-over-ranks timing reduction are the only collectives.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 256
+SLICES = 64
+N_ITER = 500
+LAM = 5e-4
+WORKLOAD = "256x256x64 slices, 500 PD iterations, lambda=5e-4 (seeds/needles phantom, elliptical mask)"
+ALG_BYTES_PER_VOXEL_ITER = 37  # read+write chi, p, qx, qy (4 x 8 B) + read dB (4 B) + mask (1 B)
+ALG_FLOPS_PER_VOXEL_ITER = 10 * 16 + 30  # 2 real 2-D FFT round trips (10 log2(HW)) + pointwise/stencil
+L2_FLUSH_BYTES = 256 << 20
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pd_cluster_kernel_256x256x64.txt")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2006_09808_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
+    try:
+        vals = {}
+        for line in open(PROFILE_SUMMARY):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(pb, tau, sigma, n_slices, n_iter):
+    """FP64 oracle on n_slices of the workload; returns (voxel-iter/s, seconds)."""
+    import numpy as np
+
+    from oracle import pd_oracle as O
+
+    f = pb.field[:n_slices].astype(np.float64)
+    m = pb.mask[:n_slices]
+    t0 = time.perf_counter()
+    for s in range(n_slices):  # the paper's CPU method: one slice after another
+        O.pd_solve(f[s], m[s], pb.lam, tau, sigma, n_iter)
+    dt = time.perf_counter() - t0
+    return n_slices * H * W * n_iter / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import phantoms
+    from oracle import pd_oracle as O
+
+    pb = phantoms.config2(SLICES)
+    L, tau, sigma = O.step_sizes(H, W)
+    n_sl, n_it = 1, 100  # bounded sample per step
+    for _ in range(args.warmup):
+        cpu_oracle_sample(pb, tau, sigma, n_sl, 10)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_sample(pb, tau, sigma, n_sl, n_it)
+        times.append(dt)
+    value = n_sl * H * W * n_it * len(times) / sum(times)
+    line = {
+        "impl": "reference",
+        "metric": "PD voxel-iterations/s",
+        "value": value,
+        "unit": "voxel-iter/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "slices": SLICES, "n_iter": N_ITER},
+        "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_sl} slice x {n_it} iterations per step of the 256x256x64 workload"},
+        "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    import paper_2006_09808_gb300 as pcs
+    import phantoms
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pcs.load_library()
+
+    # every rank solves its own volume (different phantom seed): weak scaling
+    pb = phantoms.volume(H, W, SLICES, seed=rank, lam=LAM, n_iter=N_ITER, name="bench")
+    field = torch.from_numpy(pb.field).to(dev)
+    mask = torch.from_numpy(pb.mask).to(dev)
+    chi = torch.empty_like(field)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ctx = pcs.pcs_create(H, W, SLICES, cluster_size=args.cluster_size, stream=stream)
+    ones = torch.ones((1, H, W), dtype=torch.uint8, device=dev)
+    L = pcs.pcs_opnorm(ctx, ones, 300)[0]  # step sizes of the pseudocode: tau = sigma = 1/L
+    tau = sigma = 1.0 / L
+
+    def step():
+        pcs.pcs_solve_slices(ctx, field, mask, LAM, tau, sigma, N_ITER, chi)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict L2 between steps (not timed)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    dev_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_step = sum(dev_ms) / len(dev_ms)
+    if dist is not None:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    work = SLICES * H * W * N_ITER  # voxel-iterations per rank per step
+    value = ws * work / (ms_step * 1e-3)
+
+    # ---- end to end through the host-buffer C entry point (pinned host memory)
+    hf = torch.from_numpy(pb.field).pin_memory().numpy()
+    hm = torch.from_numpy(pb.mask).pin_memory().numpy()
+    hc = torch.empty(pb.field.shape, dtype=torch.float32).pin_memory().numpy()
+    pcs.pcs_solve_slices_host(ctx, hf, hm, LAM, tau, sigma, N_ITER, hc)  # warm the staging buffers
+    e2e_t = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pcs.pcs_solve_slices_host(ctx, hf, hm, LAM, tau, sigma, N_ITER, hc)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t) / len(e2e_t)
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    dev_chi = chi.cpu().numpy()
+    assert np.array_equal(dev_chi, hc), "host-buffer path differs from the device path"
+    pcs.pcs_destroy(ctx)
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        hbm_peak = float(peaks["hbm_gbs"])
+        achieved = ALG_BYTES_PER_VOXEL_ITER * work / (ms_step * 1e-3) / 1e9
+        clocks = clk.summary()
+        fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12  # TFLOP/s at the maximum SM clock
+        alu_achieved = ALG_FLOPS_PER_VOXEL_ITER * work / (ms_step * 1e-3) / 1e12
+        traffic = profiled_traffic()
+        line = {
+            "metric": "PD voxel-iterations/s",
+            "value": value,
+            "unit": "voxel-iter/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": max(args.warmup, 3),
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": WORKLOAD, "H": H, "W": W, "slices": SLICES, "n_iter": N_ITER, "lambda": LAM,
+                "parallelism": f"slices-dp{ws}", "l2": "flushed between steps (256 MiB device write)",
+                "cluster_size": args.cluster_size or "default",
+            },
+            "roofline": {
+                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "alg_bytes_per_voxel_iter": ALG_BYTES_PER_VOXEL_ITER,
+                "fp32_alu": {"achieved_tflops": alu_achieved, "peak_tflops": fp32_peak,
+                             "frac": alu_achieved / fp32_peak,
+                             "alg_flops_per_voxel_iter": ALG_FLOPS_PER_VOXEL_ITER},
+            },
+            "e2e": {"value": ws * work / e2e_s, "unit": "voxel-iter/s",
+                    "h2d_bytes_per_step": int(pb.field.nbytes + pb.mask.nbytes),
+                    "d2h_bytes_per_step": int(pb.field.nbytes)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "wall_s_timed_region": t_wall,
+            "L": L,
+        }
+        if not args.no_cpu_baseline:
+            from oracle import pd_oracle as O  # noqa: F401  (cpu_baseline leg only)
+
+            cv, dt = cpu_oracle_sample(pb, tau, sigma, 4, N_ITER)
+            line["cpu_baseline"] = {"value": cv, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"4 slices x {N_ITER} iterations of this workload ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cluster-size", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -213,7 +213,7 @@ def volume(
     return SliceProblem(
         name=name or f"vol-{H}x{W}x{S}-seed{seed}",
         field=field.astype(np.float32),
-        mask=np.broadcast_to(mask2, (S, H, W)).astype(np.uint8),
+        mask=np.ascontiguousarray(np.broadcast_to(mask2, (S, H, W)), dtype=np.uint8),
         chi_true=chi.astype(np.float32),
         lam=lam,
         n_iter=n_iter,
