@@ -157,6 +157,29 @@ PCS_API pcs_status pcs_report(pcs_ctx *ctx, const float *field, const unsigned c
 PCS_API pcs_status pcs_opnorm(pcs_ctx *ctx, const unsigned char *mask, int S, int power_iters,
                       double *L_out);
 
+/*
+ * Solve without allocating device memory (the paper has no counterpart; this
+ * is a deployment aid).  For callers that may not call cudaMalloc once they
+ * run -- e.g. a reconstruction plug-in inside a scanner or interventional host
+ * application that owns the GPU memory budget, or code running inside another
+ * framework's memory pool -- and so cannot use pcs_create.
+ *
+ * Same iteration and arguments as pcs_solve_slices (H, W, b0_axis and the
+ * stream given per call instead of through a context).  Its scratch (dual
+ * variables, chibar, kernel tables) lives in static device arrays of fixed
+ * size that every GPU loading libpcs holds until process exit (~16.5 MiB):
+ * S*H*W may not exceed PCS_NOALLOC_MAX_VOXELS; larger calls fail with
+ * PCS_EINVAL and a message.  The first call on a device sets that device up
+ * (looks up the arrays' addresses, sets kernel attributes): make it before
+ * any stream capture.  All calls share the arrays and each leaves its state
+ * in them; calls that overlap on the GPU race and must be serialised by the
+ * caller.  Calls no allocating CUDA or library routine.
+ */
+#define PCS_NOALLOC_MAX_VOXELS 1048576
+PCS_API pcs_status pcs_solve_slices_noalloc(const float *field, const unsigned char *mask, int H, int W,
+                                            int S, double lambda, double tau, double sigma, int n_iter,
+                                            float *chi_out, int b0_axis, void *cuda_stream);
+
 /* Release the context and everything it owns. NULL-safe. */
 PCS_API void pcs_destroy(pcs_ctx *ctx);
 

@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_slices_host": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_report": (i, [vp, vp, vp, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
+        "pcs_solve_slices_noalloc": (i, [vp, vp, i, i, i, d, d, d, i, vp, i, vp]),
         "pcs_destroy": (None, [vp]),
         "pcs_last_error": (ctypes.c_char_p, []),
     }
@@ -196,6 +197,21 @@ def pcs_opnorm(ctx, mask, power_iters: int = 200):
     out = (ctypes.c_double * S)()
     _check(load_library().pcs_opnorm(ctx, m, S, power_iters, out), "pcs_opnorm")
     return list(out)
+
+
+def pcs_solve_slices_noalloc(field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out,
+                             b0_axis: int = 0, stream=None):
+    """Solve without any device allocation by the library (static scratch of
+    PCS_NOALLOC_MAX_VOXELS voxels shared by all calls; see include/pcs.h)."""
+    import torch
+
+    S, H, W = field.shape
+    f = _dev_ptr(field, "float32", (S, H, W), "field")
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(load_library().pcs_solve_slices_noalloc(f, m, H, W, S, lam, tau, sigma, n_iter, c, b0_axis,
+                                                   ctypes.c_void_p(s)), "pcs_solve_slices_noalloc")
 
 
 def pcs_destroy(ctx):

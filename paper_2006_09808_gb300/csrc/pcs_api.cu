@@ -66,6 +66,11 @@ const pcs::KernelEntry* find_entry(int H, int W, int cluster_size) {
 
 }  // namespace
 
+namespace pcs {
+// error text for the other translation units of the library
+pcs_status set_last_error(pcs_status st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace pcs
+
 // ------------------------------------------------------------------ tables (FP64 on the host)
 
 namespace pcs {
