@@ -216,7 +216,8 @@ def run_native(args):
     chi = torch.empty_like(field)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    ctx = pcs.pcs_create(H, W, SLICES, cluster_size=args.cluster_size, stream=stream)
+    ctx = pcs.pcs_create(H, W, SLICES, cluster_size=args.cluster_size, max_clusters=args.max_clusters,
+                         stream=stream)
     ones = torch.ones((1, H, W), dtype=torch.uint8, device=dev)
     L = pcs.pcs_opnorm(ctx, ones, 300)[0]  # step sizes of the pseudocode: tau = sigma = 1/L
     tau = sigma = 1.0 / L
@@ -301,6 +302,7 @@ def run_native(args):
                 "workload": WORKLOAD, "H": H, "W": W, "slices": SLICES, "n_iter": N_ITER, "lambda": LAM,
                 "parallelism": f"slices-dp{ws}", "l2": "flushed between steps (256 MiB device write)",
                 "cluster_size": args.cluster_size or "default",
+                "max_clusters": args.max_clusters or "all resident",
             },
             "roofline": {
                 "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -339,6 +341,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cluster-size", type=int, default=0)
+    ap.add_argument("--max-clusters", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

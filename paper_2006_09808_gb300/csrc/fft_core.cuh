@@ -15,10 +15,11 @@
 // 8-byte word per 16), which keeps the strided stores of a stage on distinct
 // banks.
 //
-// Twiddles come from a table tw[m] = exp(-2 pi i m / NTW) (host FP64,
-// rounded to FP32) held in shared memory; a transform of length N uses every
-// (NTW/N)-th entry (TWS = NTW / N).  Inverse transforms use conjugates and
-// are unnormalised.
+// Twiddles come from per-stage tables in shared memory laid out [r-1][k]
+// (entry W_{Ns R}^{r k}), so the lanes of a group, which hold consecutive k,
+// read consecutive words: no bank conflicts.  The tables are copied at kernel
+// start from the master table tw[m] = exp(-2 pi i m / NTW) (host FP64, rounded
+// to FP32).  Inverse transforms use conjugates and are unnormalised.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -138,15 +139,42 @@ template <> struct Plan<128, 16> { static constexpr int R1 = 16, RM = 0,  RL = 8
 template <> struct Plan<256, 16> { static constexpr int R1 = 16, RM = 0,  RL = 16; };
 template <> struct Plan<512, 16> { static constexpr int R1 = 16, RM = 16, RL = 2; };
 
-// Twiddle the legs of one butterfly of a stage with span NS and radix R.
-template <int N, int R, int NS, bool INV, int TWS>
-__device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __restrict__ tw) {
+// Per-stage twiddle tables of one transform length: the middle stage's
+// (span R1, radix RM) entries first, then the last stage's (span N/RL, radix RL).
+template <int N, int E>
+struct StageTw {
+    using PL = Plan<N, E>;
+    static constexpr int MID = PL::RM ? (PL::RM - 1) * PL::R1 : 0;
+    static constexpr int LAST = (PL::RL - 1) * (N / PL::RL);
+    static constexpr int SIZE = MID + LAST;
+    // dst[(r-1) NS + k] = W_{NS R}^{r k} = tw[r k (N / (NS R)) TWS], TWS = NTW / N
+    __device__ static void fill(float2* dst, const float2* __restrict__ tw, int TWS, int tid, int nthr) {
+        if constexpr (MID > 0) {
+            constexpr int NS = PL::R1, R = PL::RM, STEP = N / (NS * R);
+            for (int t = tid; t < MID; t += nthr) {
+                const int r = t / NS + 1, k = t % NS;
+                dst[t] = tw[(r * k * STEP) * TWS];
+            }
+        }
+        {
+            constexpr int NS = N / PL::RL, R = PL::RL, STEP = N / (NS * R);
+            for (int t = tid; t < LAST; t += nthr) {
+                const int r = t / NS + 1, k = t % NS;
+                dst[MID + t] = tw[(r * k * STEP) * TWS];
+            }
+        }
+    }
+};
+
+// Twiddle the legs of one butterfly of a stage with span NS and radix R
+// (stw: that stage's [r-1][k] table).
+template <int R, int NS, bool INV>
+__device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __restrict__ stw) {
     if constexpr (NS > 1) {
         const int k = j & (NS - 1);
-        constexpr int STEP = N / (NS * R);
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            float2 w = tw[(r * k * STEP) * TWS];
+            float2 w = stw[(r - 1) * NS + k];
             if (INV) w.y = -w.y;
             v[r] = cmul(v[r], w);
         }
@@ -155,10 +183,10 @@ __device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __r
 
 // Complex FFT of length N by a group of T lanes (lane g, group mask gm).
 // x: E = N/T elements, element g + T*e in x[e]; buf: group-private padded
-// buffer of P(N-1)+1 entries (contents destroyed).
-template <int N, int T, bool INV, int TWS>
+// buffer of P(N-1)+1 entries (contents destroyed); stw: StageTw<N, E> table.
+template <int N, int T, bool INV>
 __device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf,
-                                    const float2* __restrict__ tw, int g, unsigned gm) {
+                                    const float2* __restrict__ stw, int g, unsigned gm) {
     constexpr int E = N / T;
     using PL = Plan<N, E>;
     constexpr int R1 = PL::R1, RM = PL::RM, RL = PL::RL;
@@ -196,7 +224,7 @@ __device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int j = g + b * T;
-            twiddle<N, RM, NS, INV, TWS>(v[b], j, tw);
+            twiddle<RM, NS, INV>(v[b], j, stw);
             dftR<RM, INV>(v[b]);
             const int k = j & (NS - 1);
             const int base = (j / NS) * NS * RM + k;
@@ -215,7 +243,7 @@ __device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf
             float2 v[RL];
 #pragma unroll
             for (int r = 0; r < RL; ++r) v[r] = buf[P(j + r * NS)];
-            twiddle<N, RL, NS, INV, TWS>(v, j, tw);
+            twiddle<RL, NS, INV>(v, j, stw + StageTw<N, E>::MID);
             dftR<RL, INV>(v);
 #pragma unroll
             for (int r = 0; r < RL; ++r) x[b + r * B] = v[r];

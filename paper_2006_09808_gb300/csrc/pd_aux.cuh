@@ -90,20 +90,8 @@ template <class G>
 __global__ void __launch_bounds__(G::NT, 1) aux_report_kernel(AuxParams prm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Ctx<G> cx;
-    cx.tbuf = reinterpret_cast<float2*>(smem_raw);
-    cx.rows = cx.tbuf + G::SM_TBUF;
-    cx.tw = cx.rows + G::SM_ROWS;
-    double* red = reinterpret_cast<double*>(cx.tw + G::SM_TW);
-    if constexpr (G::C == 1) {
-        cx.crank = 0;
-        cx.tb[0] = cx.tbuf;
-    } else {
-        cg::cluster_group cluster = cg::this_cluster();
-        cx.crank = (int)cluster.block_rank();
-#pragma unroll
-        for (int q = 0; q < G::C; ++q) cx.tb[q] = cluster.map_shared_rank(cx.tbuf, q);
-    }
-    for (int t = threadIdx.x; t < G::NTW; t += G::NT) cx.tw[t] = prm.twid[t];
+    ctx_init<G>(cx, smem_raw, prm.twid);
+    double* red = reinterpret_cast<double*>(cx.stw_c + G::SM_STW_C);
     // every CTA of the cluster must have started before its shared memory is written remotely
     cluster_barrier<G::C>();
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
@@ -234,21 +222,9 @@ template <class G>
 __global__ void __launch_bounds__(G::NT, 1) aux_opnorm_kernel(AuxParams prm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Ctx<G> cx;
-    cx.tbuf = reinterpret_cast<float2*>(smem_raw);
-    cx.rows = cx.tbuf + G::SM_TBUF;
-    cx.tw = cx.rows + G::SM_ROWS;
-    double* red = reinterpret_cast<double*>(cx.tw + G::SM_TW);
+    ctx_init<G>(cx, smem_raw, prm.twid);
+    double* red = reinterpret_cast<double*>(cx.stw_c + G::SM_STW_C);
     double* slot = red + 32;
-    if constexpr (G::C == 1) {
-        cx.crank = 0;
-        cx.tb[0] = cx.tbuf;
-    } else {
-        cg::cluster_group cluster = cg::this_cluster();
-        cx.crank = (int)cluster.block_rank();
-#pragma unroll
-        for (int q = 0; q < G::C; ++q) cx.tb[q] = cluster.map_shared_rank(cx.tbuf, q);
-    }
-    for (int t = threadIdx.x; t < G::NTW; t += G::NT) cx.tw[t] = prm.twid[t];
     cluster_barrier<G::C>();
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

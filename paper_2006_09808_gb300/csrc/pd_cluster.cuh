@@ -88,7 +88,9 @@ struct Geo {
     static constexpr int SM_TBUF = MC * HP;
     static constexpr int SM_ROWS = RPP * MP;
     static constexpr int SM_TW = NTW;
-    static constexpr size_t SMEM_BYTES = sizeof(float2) * (SM_TBUF + SM_ROWS + SM_TW);
+    static constexpr int SM_STW_R = StageTw<M, ER>::SIZE;  // row-transform stage twiddles
+    static constexpr int SM_STW_C = StageTw<H, EC>::SIZE;  // column-transform stage twiddles
+    static constexpr size_t SMEM_BYTES = sizeof(float2) * (SM_TBUF + SM_ROWS + SM_TW + SM_STW_R + SM_STW_C);
 
     static_assert(TR <= 32 && TC <= 32, "group fits a warp");
     static_assert(R % RPP == 0, "row passes");
@@ -120,9 +122,33 @@ struct Ctx {
     float2* tbuf;     // own spectrum columns, [MC][HP]
     float2* rows;     // row scratch, [RPP][MP]
     float2* tw;       // twiddles [NTW]
+    float2* stw_r;    // stage twiddles of the row transforms
+    float2* stw_c;    // stage twiddles of the column transforms
     float2* tb[G::C]; // spectrum columns of every CTA of the cluster (DSMEM)
     int crank;
 };
+
+// Carve the shared-memory layout and load the twiddle tables (no barrier).
+template <class G>
+__device__ __forceinline__ void ctx_init(Ctx<G>& cx, unsigned char* smem_raw, const float2* __restrict__ twid) {
+    cx.tbuf = reinterpret_cast<float2*>(smem_raw);
+    cx.rows = cx.tbuf + G::SM_TBUF;
+    cx.tw = cx.rows + G::SM_ROWS;
+    cx.stw_r = cx.tw + G::SM_TW;
+    cx.stw_c = cx.stw_r + G::SM_STW_R;
+    for (int t = threadIdx.x; t < G::NTW; t += G::NT) cx.tw[t] = twid[t];
+    StageTw<G::M, G::ER>::fill(cx.stw_r, twid, G::NTW / G::M, threadIdx.x, G::NT);
+    StageTw<G::H, G::EC>::fill(cx.stw_c, twid, G::NTW / G::H, threadIdx.x, G::NT);
+    if constexpr (G::C == 1) {
+        cx.crank = 0;
+        cx.tb[0] = cx.tbuf;
+    } else {
+        cg::cluster_group cluster = cg::this_cluster();
+        cx.crank = (int)cluster.block_rank();
+#pragma unroll
+        for (int q = 0; q < G::C; ++q) cx.tb[q] = cluster.map_shared_rank(cx.tbuf, q);
+    }
+}
 
 // ------------------------------------------------------------------ column pass
 // Forward column FFT, multiply by D/(HW), inverse column FFT, in place on the
@@ -130,7 +156,7 @@ struct Ctx {
 template <class G>
 __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __restrict__ dtab,
                                             const float* __restrict__ ddtab) {
-    constexpr int H = G::H, TC = G::TC, EC = G::EC, NTW = G::NTW;
+    constexpr int H = G::H, TC = G::TC, EC = G::EC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % TC;
     const int grp = warp * (32 / TC) + lane / TC;
@@ -143,7 +169,7 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __res
         float2 x[EC];
 #pragma unroll
         for (int e = 0; e < EC; ++e) x[e] = col[P(g + TC * e)];
-        fft<H, TC, false, NTW / H>(x, col, cx.tw, g, gm);
+        fft<H, TC, false>(x, col, cx.stw_c, g, gm);
         if (kx != 0) {
             const float* d = dtab + (size_t)kx * H;
 #pragma unroll
@@ -161,7 +187,7 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __res
                 x[e] = make_float2(fmaf(dm, x[e].x, dd * ym.x), fmaf(dm, x[e].y, -dd * ym.y));
             }
         }
-        fft<H, TC, true, NTW / H>(x, col, cx.tw, g, gm);
+        fft<H, TC, true>(x, col, cx.stw_c, g, gm);
 #pragma unroll
         for (int e = 0; e < EC; ++e) col[P(g + TC * e)] = x[e];
         __syncwarp(gm);
@@ -176,12 +202,17 @@ template <class G>
 __device__ __forceinline__ void row_inverse(const Ctx<G>& cx, float2* rs, int i, int g, unsigned gm,
                                             float2 (&x)[G::ER]) {
     constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
+    {
+        float2 t[ER];  // all remote loads in flight before any local store
 #pragma unroll
-    for (int e = 0; e < ER; ++e) {
-        const int k = g + TR * e;
-        const int q = (TR * e) / MC;  // compile-time after unrolling
-        const int cl = k - q * MC;
-        rs[P(k)] = cx.tb[q][cl * G::HP + P(i)];
+        for (int e = 0; e < ER; ++e) {
+            const int k = g + TR * e;
+            const int q = (TR * e) / MC;  // compile-time after unrolling
+            const int cl = k - q * MC;
+            t[e] = cx.tb[q][cl * G::HP + P(i)];
+        }
+#pragma unroll
+        for (int e = 0; e < ER; ++e) rs[P(g + TR * e)] = t[e];
     }
     __syncwarp(gm);
 #pragma unroll
@@ -200,7 +231,7 @@ __device__ __forceinline__ void row_inverse(const Ctx<G>& cx, float2* rs, int i,
             x[e] = make_float2(ec.x - od.y, ec.y + od.x);  // ec + i od
         }
     }
-    fft<M, TR, true, NTW / M>(x, rs, cx.tw, g, gm);
+    fft<M, TR, true>(x, rs, cx.stw_r, g, gm);
 }
 
 // Forward real row transform of z[e] = (x[2n], x[2n+1]), n = g + TR*e, and
@@ -209,7 +240,7 @@ template <class G>
 __device__ __forceinline__ void row_forward(const Ctx<G>& cx, float2* rs, int i, int g, unsigned gm,
                                             float2 (&z)[G::ER]) {
     constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
-    fft<M, TR, false, NTW / M>(z, rs, cx.tw, g, gm);
+    fft<M, TR, false>(z, rs, cx.stw_r, g, gm);
 #pragma unroll
     for (int e = 0; e < ER; ++e) rs[P(g + TR * e)] = z[e];
     __syncwarp(gm);
@@ -238,108 +269,152 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, float2* rs, int i,
 
 // ------------------------------------------------------------------ row phases
 
+// Epilogue element chunk: the loads of CH elements are issued together, then
+// computed and stored (restrict-qualified pointers let the next chunk's loads
+// move ahead of this chunk's stores).
+constexpr int kChunk = 4;
+
 // Phase B: u = D chibar -> dual proxes -> forward transform of W p.
+// q and p stay exactly zero wherever the 0/1 mask is zero (zero start, masked
+// increments), so W p = p and M q = q: the adjoint transform takes p as is.
 template <class G>
 __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm, size_t base) {
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
+    constexpr int CH = (ER < kChunk) ? ER : kChunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % TR;
     const int grp = warp * (32 / TR) + lane / TR;
     const unsigned gm = group_mask<TR>(lane);
+    const int src_right = (g == TR - 1) ? lane - (TR - 1) : lane + 1;  // lane holding pixel 2n+2
     float2* rs = cx.rows + grp * G::MP;
     const float sigma = prm.sigma, inv_den = prm.inv_den;
+    const float* __restrict__ fld = prm.field;
+    const unsigned char* __restrict__ msk = prm.mask;
+    const float* __restrict__ cbar = prm.chibar;
+    float* __restrict__ pp = prm.p;
+    float* __restrict__ qxp = prm.qx;
+    float* __restrict__ qyp = prm.qy;
 #pragma unroll 1
     for (int pass = 0; pass < G::R / G::RPP; ++pass) {
         const int i = cx.crank * G::R + pass * G::RPP + grp;
-        float2 x[ER];
-        row_inverse<G>(cx, rs, i, g, gm, x);
         const size_t rowoff = base + (size_t)i * W;
         const bool has_down = (i + 1 < H);
+        // chibar of this row; its right neighbours come from the next lane by shuffle
+        float2 cb[ER];
 #pragma unroll
-        for (int e = 0; e < ER; ++e) {
-            const int n = g + TR * e;
-            const int j0 = 2 * n;
-            const size_t o = rowoff + j0;
-            const float2 u = x[e];
-            const float2 f = __ldg(reinterpret_cast<const float2*>(prm.field + o));
-            const uchar2 mk = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o));
-            const float m0 = (float)mk.x, m1 = (float)mk.y;
-            float2 p = __ldcg(reinterpret_cast<const float2*>(prm.p + o));
-            // dual data prox (W = mask, W dB computed on the fly)
-            p.x = (p.x + sigma * (m0 * (u.x - f.x))) * inv_den;
-            p.y = (p.y + sigma * (m1 * (u.y - f.y))) * inv_den;
-            __stcg(reinterpret_cast<float2*>(prm.p + o), p);
-            // dual TV prox (forward differences of chibar, Neumann boundary)
-            const float2 cb = __ldcg(reinterpret_cast<const float2*>(prm.chibar + o));
-            const float cr = (j0 + 2 < W) ? __ldcg(prm.chibar + o + 2) : cb.y;
-            float2 cd = cb;
-            if (has_down) cd = __ldcg(reinterpret_cast<const float2*>(prm.chibar + o + W));
-            float2 qx = __ldcg(reinterpret_cast<const float2*>(prm.qx + o));
-            float2 qy = __ldcg(reinterpret_cast<const float2*>(prm.qy + o));
-            qx.x = fminf(1.f, fmaxf(-1.f, qx.x + sigma * m0 * (cb.y - cb.x)));
-            qx.y = fminf(1.f, fmaxf(-1.f, qx.y + sigma * m1 * (cr - cb.y)));
-            qy.x = fminf(1.f, fmaxf(-1.f, qy.x + sigma * m0 * (cd.x - cb.x)));
-            qy.y = fminf(1.f, fmaxf(-1.f, qy.y + sigma * m1 * (cd.y - cb.y)));
-            __stcg(reinterpret_cast<float2*>(prm.qx + o), qx);
-            __stcg(reinterpret_cast<float2*>(prm.qy + o), qy);
-            x[e] = make_float2(m0 * p.x, m1 * p.y);  // W p: input of the adjoint transform
+        for (int e = 0; e < ER; ++e) cb[e] = __ldcg(reinterpret_cast<const float2*>(cbar + rowoff + 2 * (g + TR * e)));
+        float2 x[ER];
+        row_inverse<G>(cx, rs, i, g, gm, x);
+        float cr[ER];
+#pragma unroll
+        for (int e = 0; e < ER; ++e) cr[e] = __shfl_sync(gm, cb[e].x, src_right);
+#pragma unroll
+        for (int e0 = 0; e0 < ER; e0 += CH) {
+            float2 f[CH], p[CH], cd[CH], qx[CH], qy[CH];
+            uchar2 mk[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const size_t o = rowoff + 2 * (g + TR * (e0 + c));
+                f[c] = __ldg(reinterpret_cast<const float2*>(fld + o));
+                mk[c] = __ldg(reinterpret_cast<const uchar2*>(msk + o));
+                p[c] = __ldcg(reinterpret_cast<const float2*>(pp + o));
+                cd[c] = has_down ? __ldcg(reinterpret_cast<const float2*>(cbar + o + W)) : cb[e0 + c];
+                qx[c] = __ldcg(reinterpret_cast<const float2*>(qxp + o));
+                qy[c] = __ldcg(reinterpret_cast<const float2*>(qyp + o));
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int e = e0 + c;
+                const size_t o = rowoff + 2 * (g + TR * e);
+                // pixel 2n+2 is in the next lane at the same e, or in lane 0 at e+1; past the
+                // last column the difference is zero (Neumann)
+                float right = cr[e];
+                if (g == TR - 1) right = (e + 1 < ER) ? cr[e + 1] : cb[e].y;
+                const float m0 = mk[c].x ? 1.f : 0.f, m1 = mk[c].y ? 1.f : 0.f;
+                const float2 u = x[e];
+                // dual data prox (W = mask, W dB formed on the fly)
+                float2 pn;
+                pn.x = (p[c].x + sigma * (m0 * (u.x - f[c].x))) * inv_den;
+                pn.y = (p[c].y + sigma * (m1 * (u.y - f[c].y))) * inv_den;
+                // dual TV prox (forward differences of chibar, Neumann boundary)
+                float2 qxn, qyn;
+                qxn.x = fminf(1.f, fmaxf(-1.f, qx[c].x + sigma * m0 * (cb[e].y - cb[e].x)));
+                qxn.y = fminf(1.f, fmaxf(-1.f, qx[c].y + sigma * m1 * (right - cb[e].y)));
+                qyn.x = fminf(1.f, fmaxf(-1.f, qy[c].x + sigma * m0 * (cd[c].x - cb[e].x)));
+                qyn.y = fminf(1.f, fmaxf(-1.f, qy[c].y + sigma * m1 * (cd[c].y - cb[e].y)));
+                __stcg(reinterpret_cast<float2*>(pp + o), pn);
+                __stcg(reinterpret_cast<float2*>(qxp + o), qxn);
+                __stcg(reinterpret_cast<float2*>(qyp + o), qyn);
+                x[e] = pn;  // W p = p: input of the adjoint transform
+            }
         }
         row_forward<G>(cx, rs, i, g, gm, x);
     }
 }
 
 // Phase A: v = D W p -> primal step -> over-relaxation -> forward transform of chibar.
+// G^T M q = G^T q because q vanishes outside the mask (see phase_dual).
 template <class G>
 __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParams& prm, size_t base,
                                              bool last) {
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
+    constexpr int CH = (ER < kChunk) ? ER : kChunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % TR;
     const int grp = warp * (32 / TR) + lane / TR;
     const unsigned gm = group_mask<TR>(lane);
+    const int src_left = (g == 0) ? lane + (TR - 1) : lane - 1;  // lane holding pixel 2n-1
     float2* rs = cx.rows + grp * G::MP;
     const float tau = prm.tau;
+    const float* __restrict__ qxp = prm.qx;
+    const float* __restrict__ qyp = prm.qy;
+    float* __restrict__ chip = prm.chi;
+    float* __restrict__ cbar = prm.chibar;
 #pragma unroll 1
     for (int pass = 0; pass < G::R / G::RPP; ++pass) {
         const int i = cx.crank * G::R + pass * G::RPP + grp;
-        float2 x[ER];
-        row_inverse<G>(cx, rs, i, g, gm, x);
         const size_t rowoff = base + (size_t)i * W;
         const bool has_up = (i > 0), has_down = (i + 1 < H);
+        float2 qx[ER];
 #pragma unroll
-        for (int e = 0; e < ER; ++e) {
-            const int n = g + TR * e;
-            const int j0 = 2 * n;
-            const size_t o = rowoff + j0;
-            const float2 v = x[e];
-            const uchar2 mk = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o));
-            const float m0 = (float)mk.x, m1 = (float)mk.y;
-            const float2 qx = __ldcg(reinterpret_cast<const float2*>(prm.qx + o));
-            const float2 qy = __ldcg(reinterpret_cast<const float2*>(prm.qy + o));
-            // a = M qx, b = M qy;  G^T(a,b)[j] = a[j-1][j>0] - a[j][j<W-1] + b[i-1][i>0] - b[i][i<H-1]
-            const float a0 = m0 * qx.x, a1 = m1 * qx.y;
-            float al = 0.f;
-            if (j0 > 0) al = (float)__ldg(prm.mask + o - 1) * __ldcg(prm.qx + o - 1);
-            const float a1r = (j0 + 2 < W) ? a1 : 0.f;  // a[j1] counts only if j1 < W-1
-            float bu0 = 0.f, bu1 = 0.f;
-            if (has_up) {
-                const uchar2 mu = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o - W));
-                const float2 qu = __ldcg(reinterpret_cast<const float2*>(prm.qy + o - W));
-                bu0 = (float)mu.x * qu.x;
-                bu1 = (float)mu.y * qu.y;
+        for (int e = 0; e < ER; ++e) qx[e] = __ldcg(reinterpret_cast<const float2*>(qxp + rowoff + 2 * (g + TR * e)));
+        float2 x[ER];
+        row_inverse<G>(cx, rs, i, g, gm, x);
+        float ql[ER];
+#pragma unroll
+        for (int e = 0; e < ER; ++e) ql[e] = __shfl_sync(gm, qx[e].y, src_left);
+#pragma unroll
+        for (int e0 = 0; e0 < ER; e0 += CH) {
+            float2 qy[CH], qu[CH], chi[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const size_t o = rowoff + 2 * (g + TR * (e0 + c));
+                qy[c] = __ldcg(reinterpret_cast<const float2*>(qyp + o));
+                qu[c] = has_up ? __ldcg(reinterpret_cast<const float2*>(qyp + o - W)) : make_float2(0.f, 0.f);
+                chi[c] = __ldcg(reinterpret_cast<const float2*>(chip + o));
             }
-            const float b0 = has_down ? m0 * qy.x : 0.f;
-            const float b1 = has_down ? m1 * qy.y : 0.f;
-            const float d0 = (al - a0) + (bu0 - b0);
-            const float d1 = (a0 - a1r) + (bu1 - b1);
-            const float2 chi = __ldcg(reinterpret_cast<const float2*>(prm.chi + o));
-            float2 cn;
-            cn.x = chi.x - tau * v.x - tau * d0;
-            cn.y = chi.y - tau * v.y - tau * d1;
-            __stcg(reinterpret_cast<float2*>(prm.chi + o), cn);
-            const float2 cb = make_float2(2.f * cn.x - chi.x, 2.f * cn.y - chi.y);
-            if (!last) __stcg(reinterpret_cast<float2*>(prm.chibar + o), cb);
-            x[e] = cb;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int e = e0 + c;
+                const int j0 = 2 * (g + TR * e);
+                const size_t o = rowoff + j0;
+                const float2 v = x[e];
+                // G^T(a,b)[j] = a[j-1][j>0] - a[j][j<W-1] + b[i-1][i>0] - b[i][i<H-1], a = qx, b = qy
+                float al = ql[e];
+                if (g == 0) al = (e > 0) ? ql[e - 1] : 0.f;
+                const float a1r = (j0 + 2 < W) ? qx[e].y : 0.f;
+                const float b0 = has_down ? qy[c].x : 0.f;
+                const float b1 = has_down ? qy[c].y : 0.f;
+                const float d0 = (al - qx[e].x) + (qu[c].x - b0);
+                const float d1 = (qx[e].x - a1r) + (qu[c].y - b1);
+                float2 cn;
+                cn.x = chi[c].x - tau * v.x - tau * d0;
+                cn.y = chi[c].y - tau * v.y - tau * d1;
+                __stcg(reinterpret_cast<float2*>(chip + o), cn);
+                const float2 cb = make_float2(2.f * cn.x - chi[c].x, 2.f * cn.y - chi[c].y);
+                if (!last) __stcg(reinterpret_cast<float2*>(cbar + o), cb);
+                x[e] = cb;
+            }
         }
         if (!last) row_forward<G>(cx, rs, i, g, gm, x);
     }
@@ -351,19 +426,7 @@ template <class G>
 __global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParams prm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Ctx<G> cx;
-    cx.tbuf = reinterpret_cast<float2*>(smem_raw);
-    cx.rows = cx.tbuf + G::SM_TBUF;
-    cx.tw = cx.rows + G::SM_ROWS;
-    if constexpr (G::C == 1) {
-        cx.crank = 0;
-        cx.tb[0] = cx.tbuf;
-    } else {
-        cg::cluster_group cluster = cg::this_cluster();
-        cx.crank = (int)cluster.block_rank();
-#pragma unroll
-        for (int q = 0; q < G::C; ++q) cx.tb[q] = cluster.map_shared_rank(cx.tbuf, q);
-    }
-    for (int t = threadIdx.x; t < G::NTW; t += G::NT) cx.tw[t] = prm.twid[t];
+    ctx_init<G>(cx, smem_raw, prm.twid);
 
     const int cid = blockIdx.x / G::C;
     const int ncl = gridDim.x / G::C;
