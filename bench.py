@@ -217,7 +217,7 @@ def run_native(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ctx = pcs.pcs_create(H, W, SLICES, cluster_size=args.cluster_size, max_clusters=args.max_clusters,
-                         stream=stream)
+                         kernel=args.kernel, threads=args.threads, stream=stream)
     ones = torch.ones((1, H, W), dtype=torch.uint8, device=dev)
     L = pcs.pcs_opnorm(ctx, ones, 300)[0]  # step sizes of the pseudocode: tau = sigma = 1/L
     tau = sigma = 1.0 / L
@@ -303,6 +303,8 @@ def run_native(args):
                 "parallelism": f"slices-dp{ws}", "l2": "flushed between steps (256 MiB device write)",
                 "cluster_size": args.cluster_size or "default",
                 "max_clusters": args.max_clusters or "all resident",
+                "kernel": {0: "default", 1: "streaming", 2: "resident"}[args.kernel],
+                "threads": args.threads or "default",
             },
             "roofline": {
                 "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -342,6 +344,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cluster-size", type=int, default=0)
     ap.add_argument("--max-clusters", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=0, help="0 default, 1 streaming, 2 resident")
+    ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

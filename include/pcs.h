@@ -67,7 +67,10 @@ typedef struct pcs_options {
     int b0_axis;       /* 0 = B0 along rows / y (default), 1 = along columns / x */
     int cluster_size;  /* 0 = library default for the slice size; else CTAs per slice (1,2,4,8,16) */
     int max_clusters;  /* 0 = as many concurrent clusters as fit; else an upper bound (tuning) */
-    int reserved[5];
+    int kernel;        /* 0 = library default; 1 = streaming (state in global memory);
+                          2 = resident (state kept on chip for all iterations) */
+    int threads;       /* 0 = library default; else threads per CTA of a compiled variant */
+    int reserved[3];
 } pcs_options;
 
 /* Diagnostics of one slice at (chi_N, p_N, q_N), in FP64 (see pcs_slice_report doc below). */

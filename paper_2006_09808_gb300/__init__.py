@@ -34,7 +34,9 @@ class pcs_options(ctypes.Structure):
         ("b0_axis", ctypes.c_int),
         ("cluster_size", ctypes.c_int),
         ("max_clusters", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("kernel", ctypes.c_int),
+        ("threads", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -137,15 +139,19 @@ def pcs_supported_size(H: int, W: int) -> bool:
     return bool(load_library().pcs_supported_size(H, W))
 
 
+KERNEL_DEFAULT, KERNEL_STREAMING, KERNEL_RESIDENT = 0, 1, 2
+
+
 def pcs_create(H: int, W: int, max_slices: int, b0_axis: int = 0, cluster_size: int = 0, max_clusters: int = 0,
-               stream=None):
+               kernel: int = KERNEL_DEFAULT, threads: int = 0, stream=None):
     """Create a context; returns an opaque handle (c_void_p).  stream: torch.cuda.Stream or None (current)."""
     import torch
 
     lib = load_library()
     opt = pcs_options()
     lib.pcs_options_default(ctypes.byref(opt))
-    opt.b0_axis, opt.cluster_size, opt.max_clusters = b0_axis, cluster_size, max_clusters
+    opt.b0_axis, opt.cluster_size, opt.max_clusters, opt.kernel = b0_axis, cluster_size, max_clusters, kernel
+    opt.threads = threads
     s = (stream or torch.cuda.current_stream()).cuda_stream
     h = ctypes.c_void_p()
     _check(lib.pcs_create(ctypes.byref(h), H, W, max_slices, ctypes.byref(opt), ctypes.c_void_p(s)), "pcs_create")

@@ -138,6 +138,10 @@ template <> struct Plan<64, 8>   { static constexpr int R1 = 8,  RM = 0,  RL = 8
 template <> struct Plan<128, 16> { static constexpr int R1 = 16, RM = 0,  RL = 8; };
 template <> struct Plan<256, 16> { static constexpr int R1 = 16, RM = 0,  RL = 16; };
 template <> struct Plan<512, 16> { static constexpr int R1 = 16, RM = 16, RL = 2; };
+// eight elements per lane: three radix-8 based stages
+template <> struct Plan<128, 8>  { static constexpr int R1 = 8,  RM = 8,  RL = 2; };
+template <> struct Plan<256, 8>  { static constexpr int R1 = 8,  RM = 8,  RL = 4; };
+template <> struct Plan<512, 8>  { static constexpr int R1 = 8,  RM = 8,  RL = 8; };
 
 // Per-stage twiddle tables of one transform length: the middle stage's
 // (span R1, radix RM) entries first, then the last stage's (span N/RL, radix RL).

@@ -57,10 +57,13 @@ const std::vector<pcs::KernelEntry>& entries() {
     return v;
 }
 
-// First entry for (H, W) is the default; cluster_size > 0 selects a variant.
-const pcs::KernelEntry* find_entry(int H, int W, int cluster_size) {
+// First matching entry for (H, W) is the default; cluster_size > 0 and
+// kernel (1 streaming, 2 resident) narrow the choice.
+const pcs::KernelEntry* find_entry(int H, int W, int cluster_size, int kernel = 0, int threads = 0) {
     for (const auto& e : entries())
-        if (e.H == H && e.W == W && (cluster_size <= 0 || e.C == cluster_size)) return &e;
+        if (e.H == H && e.W == W && (cluster_size <= 0 || e.C == cluster_size) &&
+            (kernel <= 0 || e.resident == (kernel == 2 ? 1 : 0)) && (threads <= 0 || e.threads == threads))
+            return &e;
     return nullptr;
 }
 
@@ -316,9 +319,11 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
     pcs_options_default(&o);
     if (opt) o = *opt;
     if (o.b0_axis != 0 && o.b0_axis != 1) return fail(PCS_EINVAL, "b0_axis must be 0 or 1");
-    const pcs::KernelEntry* entry = find_entry(H, W, o.cluster_size);
+    if (o.kernel < 0 || o.kernel > 2) return fail(PCS_EINVAL, "kernel must be 0, 1 or 2");
+    const pcs::KernelEntry* entry = find_entry(H, W, o.cluster_size, o.kernel, o.threads);
     if (!entry)
-        return fail(PCS_EUNSUPPORTED, "no kernel for %d x %d slices with cluster_size %d", H, W, o.cluster_size);
+        return fail(PCS_EUNSUPPORTED, "no kernel for %d x %d slices with cluster_size %d, kernel %d, threads %d", H,
+                    W, o.cluster_size, o.kernel, o.threads);
 
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);

@@ -3,6 +3,7 @@
 
 namespace pcs {
 static const KernelEntry k_entries[] = {
+    make_resident_entry<GeoRes<128, 128, 4>>(),
     make_entry<Geo<128, 128, 1, 2>>(),
     make_entry<Geo<128, 128, 2, 2>>(),
 };

@@ -3,6 +3,7 @@
 
 namespace pcs {
 static const KernelEntry k_entries[] = {
+    make_resident_entry<GeoRes<64, 64, 1>>(),
     make_entry<Geo<64, 64, 1, 2>>(),
 };
 const KernelEntry* entries_64(int* n) {

@@ -66,7 +66,9 @@ constexpr int ceil_to_mod16(int v, int want) {  // smallest x >= v with x % 16 =
     return v + ((want % 16) - (v % 16) + 16) % 16;
 }
 
-template <int H_, int W_, int C_, int MINB_ = 1, int NT_ = 256>
+// ER_, EC_: elements per lane of the row / column transforms (0 = 16 for
+// lengths >= 128, else 8).
+template <int H_, int W_, int C_, int MINB_ = 1, int NT_ = 256, int ER_ = 0, int EC_ = 0>
 struct Geo {
     static constexpr int H = H_, W = W_, C = C_, NT = NT_, MINB = MINB_;
     static constexpr int M = W / 2;    // complex row length (packed half spectrum)
@@ -74,10 +76,10 @@ struct Geo {
     static constexpr int MC = M / C;   // spectrum columns per CTA
     static constexpr int NTW = (H > W) ? H : W;
     // row transforms (length M)
-    static constexpr int ER = (M >= 128) ? 16 : 8;
+    static constexpr int ER = ER_ ? ER_ : ((M >= 128) ? 16 : 8);
     static constexpr int TR = M / ER;
     // column transforms (length H)
-    static constexpr int EC = (H >= 128) ? 16 : 8;
+    static constexpr int EC = EC_ ? EC_ : ((H >= 128) ? 16 : 8);
     static constexpr int TC = H / EC;
     static constexpr int NW = NT / 32;
     static constexpr int RPP = NW * (32 / TR);  // rows in flight per CTA
@@ -94,7 +96,8 @@ struct Geo {
 
     static_assert(TR <= 32 && TC <= 32, "group fits a warp");
     static_assert(R % RPP == 0, "row passes");
-    static_assert(MC % CPP == 0, "column passes");
+    static_assert(MC % CPP == 0 || CPP % MC == 0, "column passes");
+    static constexpr int CPASSES = (MC >= CPP) ? MC / CPP : 1;  // groups beyond MC idle
     static_assert(MC % TR == 0, "gather/scatter owner is compile-time per element");
     static_assert(W % 4 == 0 && H % 16 == 0, "shape");
 };
@@ -162,8 +165,9 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __res
     const int grp = warp * (32 / TC) + lane / TC;
     const unsigned gm = group_mask<TC>(lane);
 #pragma unroll 1
-    for (int pass = 0; pass < G::MC / G::CPP; ++pass) {
+    for (int pass = 0; pass < G::CPASSES; ++pass) {
         const int cl = pass * G::CPP + grp;
+        if (G::CPP > G::MC && cl >= G::MC) break;  // whole group idles (uniform per group)
         const int kx = cx.crank * G::MC + cl;
         float2* col = cx.tbuf + cl * G::HP;
         float2 x[EC];

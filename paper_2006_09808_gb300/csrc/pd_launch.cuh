@@ -5,6 +5,7 @@
 
 #include "pd_aux.cuh"
 #include "pd_cluster.cuh"
+#include "pd_resident.cuh"
 
 namespace pcs {
 
@@ -12,6 +13,7 @@ namespace pcs {
 // diagnostics / step-size companions.
 struct KernelEntry {
     int H, W, C;
+    int resident;  // 1: state held on chip (pd_resident_kernel); 0: state streamed (pd_cluster_kernel)
     size_t smem;
     int threads;
     // Sets function attributes; returns how many clusters of the iteration
@@ -92,9 +94,34 @@ cudaError_t prepare_all(int* max_clusters, int* max_clusters_aux) {
 
 template <class G>
 constexpr KernelEntry make_entry() {
-    return KernelEntry{G::H,           G::W,           G::C,
+    return KernelEntry{G::H,           G::W,           G::C,       0,
                        G::SMEM_BYTES,  G::NT,          &prepare_all<G>,
                        &launch_pd<G>,  &launch_report<G>, &launch_opnorm<G>};
+}
+
+// Resident variant: the iteration kernel keeps the state on chip; the
+// diagnostics and power iteration use the streaming geometry's kernels.
+template <class GR>
+cudaError_t launch_res(const PDParams& prm, int n_clusters, cudaStream_t stream) {
+    return launch_cluster<GR>(pd_resident_kernel<GR>, prm, GR::SMEM_BYTES, n_clusters, stream);
+}
+template <class GR>
+cudaError_t prepare_res(int* max_clusters, int* max_clusters_aux) {
+    using G = typename GR::B;
+    cudaError_t e = prepare_cluster<GR>(pd_resident_kernel<GR>, GR::SMEM_BYTES, max_clusters);
+    if (e != cudaSuccess) return e;
+    int a = 0, b = 0;
+    if ((e = prepare_cluster<G>(aux_report_kernel<G>, aux_smem<G>(), &a)) != cudaSuccess) return e;
+    if ((e = prepare_cluster<G>(aux_opnorm_kernel<G>, aux_smem<G>(), &b)) != cudaSuccess) return e;
+    *max_clusters_aux = a < b ? a : b;
+    return cudaSuccess;
+}
+template <class GR>
+constexpr KernelEntry make_resident_entry() {
+    using G = typename GR::B;
+    return KernelEntry{GR::H,           GR::W,          GR::C,       1,
+                       GR::SMEM_BYTES,  GR::NT,         &prepare_res<GR>,
+                       &launch_res<GR>, &launch_report<G>, &launch_opnorm<G>};
 }
 
 // Per-size translation units define these (pd_<size>.cu).

@@ -35,8 +35,25 @@ def _built():
 
 
 @functools.lru_cache(maxsize=None)
-def steps(H, W):
-    return O.step_sizes(H, W)
+def _golden_L():
+    import os
+
+    table = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "opnorm_full_mask.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            H, W, ax, L = line.split()
+            table[(int(H), int(W), int(ax))] = float(L)
+    return table
+
+
+def steps(H, W, b0_axis=0):
+    """(L, tau, sigma) = (||K||, 1/L, 1/L) of the full-mask operator, from the
+    oracle-written table (tests/golden/make_step_sizes.py), else the oracle."""
+    L = _golden_L().get((H, W, b0_axis))
+    if L is None:
+        L = O.opnorm(np.ones((H, W)), b0_axis=b0_axis)
+    return L, 1.0 / L, 1.0 / L
 
 
 def rel_l2(a, b, mask=None):
@@ -87,24 +104,53 @@ def test_parity_64_regimes(lam):
         assert rel_l2(got[s], ref[s]) <= TOL, s
 
 
-@pytest.mark.parametrize("cluster_size", [1, 2])
-def test_parity_128(cluster_size):
+STREAMING, RESIDENT = pcs.KERNEL_STREAMING, pcs.KERNEL_RESIDENT
+
+
+@pytest.mark.parametrize("kernel,cluster_size", [(RESIDENT, 4), (STREAMING, 1), (STREAMING, 2)])
+def test_parity_128(kernel, cluster_size):
     pb = phantoms.volume(128, 128, 3, seed=5, lam=5e-4, n_iter=200)
     L, tau, sigma = steps(128, 128)
     ref = oracle_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter)
-    got = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, cluster_size=cluster_size)
+    got = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, cluster_size=cluster_size, kernel=kernel)
     for s in range(3):
         assert rel_l2(got[s], ref[s]) <= TOL, s
 
 
-@pytest.mark.parametrize("cluster_size", [2, 4, 8])
-def test_parity_256_cluster_variants(cluster_size):
+@pytest.mark.parametrize(
+    "kernel,cluster_size,threads",
+    [(RESIDENT, 8, 256), (RESIDENT, 8, 512), (STREAMING, 2, 256), (STREAMING, 4, 256), (STREAMING, 4, 512),
+     (STREAMING, 8, 256)],
+)
+def test_parity_256_kernel_variants(kernel, cluster_size, threads):
     pb = phantoms.volume(256, 256, 2, seed=21, lam=5e-4, n_iter=100)
     L, tau, sigma = steps(256, 256)
     ref = oracle_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter)
-    got = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, cluster_size=cluster_size)
+    got = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, cluster_size=cluster_size, kernel=kernel,
+                    threads=threads)
     for s in range(2):
         assert rel_l2(got[s], ref[s]) <= TOL, s
+
+
+@pytest.mark.parametrize("kernel", [RESIDENT, STREAMING])
+def test_parity_64_kernels_ragged_mask(kernel):
+    rng = np.random.default_rng(12)
+    pb = phantoms.volume(64, 64, 3, seed=13, lam=0.5, n_iter=150)
+    mask = (rng.random(pb.mask.shape) > 0.2).astype(np.uint8) * pb.mask
+    L, tau, sigma = steps(64, 64)
+    ref = oracle_solve(pb.field, mask, pb.lam, tau, sigma, pb.n_iter)
+    got = gpu_solve(pb.field, mask, pb.lam, tau, sigma, pb.n_iter, kernel=kernel)
+    for s in range(3):
+        assert rel_l2(got[s], ref[s]) <= TOL, s
+
+
+def test_resident_and_streaming_kernels_agree_at_full_size():
+    pb = phantoms.volume(256, 256, 16, seed=31, lam=5e-4, n_iter=200)
+    L, tau, sigma = steps(256, 256)
+    a = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, kernel=RESIDENT)
+    b = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, kernel=STREAMING)
+    for s in range(16):
+        assert rel_l2(a[s], b[s]) <= 1e-5, s
 
 
 def test_config2_full_size_sampled_slices():
@@ -131,7 +177,7 @@ def test_parity_512():
 
 def test_b0_along_columns():
     pb = phantoms.volume(64, 64, 2, seed=8, lam=1.0, n_iter=120)
-    L = O.opnorm(np.ones((64, 64)), b0_axis=1)
+    L, _, _ = steps(64, 64, b0_axis=1)
     ref = O.pd_solve(pb.field.astype(np.float64), pb.mask, pb.lam, 1 / L, 1 / L, pb.n_iter, b0_axis=1)
     got = gpu_solve(pb.field, pb.mask, pb.lam, 1 / L, 1 / L, pb.n_iter, b0_axis=1)
     assert rel_l2(got, ref) <= TOL
@@ -140,17 +186,18 @@ def test_b0_along_columns():
 # --------------------------------------------------------------------------- structure and edge cases
 
 
-def test_batch_invariance_bitwise():
+@pytest.mark.parametrize("kernel", [RESIDENT, STREAMING])
+def test_batch_invariance_bitwise(kernel):
     """A slice gives bit-identical chi alone, inside a batch, and at another batch position."""
     pb = phantoms.volume(256, 256, 6, seed=2, lam=5e-4, n_iter=40)
     L, tau, sigma = steps(256, 256)
-    batch = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter)
-    alone = gpu_solve(pb.field[4:5], pb.mask[4:5], pb.lam, tau, sigma, pb.n_iter)
+    batch = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, kernel=kernel)
+    alone = gpu_solve(pb.field[4:5], pb.mask[4:5], pb.lam, tau, sigma, pb.n_iter, kernel=kernel)
     assert np.array_equal(batch[4], alone[0])
     perm = [4, 0, 1, 2, 3, 5]
-    shuffled = gpu_solve(pb.field[perm], pb.mask[perm], pb.lam, tau, sigma, pb.n_iter)
+    shuffled = gpu_solve(pb.field[perm], pb.mask[perm], pb.lam, tau, sigma, pb.n_iter, kernel=kernel)
     assert np.array_equal(shuffled[0], batch[4])
-    few = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, max_clusters=1)
+    few = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, max_clusters=1, kernel=kernel)
     assert np.array_equal(few, batch)
 
 

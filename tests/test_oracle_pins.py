@@ -318,6 +318,17 @@ def test_opnorm_matches_dense_spectral_norm(H, W, seed):
     assert O.opnorm(m, rtol=1e-14) == pytest.approx(np.linalg.norm(K, 2), rel=1e-7)
 
 
+def test_golden_step_size_table_is_the_oracles():
+    import os
+
+    path = os.path.join(GOLDEN, "opnorm_full_mask.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for H, W, ax, L in rows:
+        if int(H) <= 64:  # recompute the cheap ones
+            assert O.opnorm(np.ones((int(H), int(W))), b0_axis=int(ax)) == pytest.approx(float(L), rel=1e-12)
+        assert 2.7 < float(L) <= math.sqrt(4.0 / 9.0 + 8.0)
+
+
 def test_opnorm_bounds_full_mask():
     # ||D|| <= 2/3 and ||G||^2 <= 8 give ||K|| <= sqrt(4/9 + 8)
     for n in (8, 32, 64):
