@@ -215,9 +215,10 @@ def run_native(args):
     mask = torch.from_numpy(pb.mask).to(dev)
     chi = torch.empty_like(field)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)  # a real stream: the solve is replayed as a captured CUDA graph
+    torch.cuda.set_stream(stream)
     ctx = pcs.pcs_create(H, W, SLICES, cluster_size=args.cluster_size, max_clusters=args.max_clusters,
-                         kernel=args.kernel, threads=args.threads, stream=stream)
+                         kernel=args.kernel, threads=args.threads, use_graph=not args.no_graph, stream=stream)
     ones = torch.ones((1, H, W), dtype=torch.uint8, device=dev)
     L = pcs.pcs_opnorm(ctx, ones, 300)[0]  # step sizes of the pseudocode: tau = sigma = 1/L
     tau = sigma = 1.0 / L
@@ -275,6 +276,27 @@ def run_native(args):
         e2e_s = float(t.item())
     dev_chi = chi.cpu().numpy()
     assert np.array_equal(dev_chi, hc), "host-buffer path differs from the device path"
+
+    # ---- the plain per-slice GPU loop (one launch per slice, one slice after another)
+    plain = None
+    if args.plain_loop:
+        ctx1 = pcs.pcs_create(H, W, 1, stream=stream)
+        chi1 = torch.empty_like(chi)
+        pcs.pcs_solve_slices(ctx1, field[:1], mask[:1], LAM, tau, sigma, N_ITER, chi1[:1])  # warm
+        flush.fill_(0.5)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s_ in range(SLICES):
+            pcs.pcs_solve_slices(ctx1, field[s_:s_ + 1], mask[s_:s_ + 1], LAM, tau, sigma, N_ITER, chi1[s_:s_ + 1])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms_plain = t0.elapsed_time(t1)
+        assert np.array_equal(chi1.cpu().numpy(), dev_chi), "per-slice loop differs from the batched solve"
+        plain = {"value": work / (ms_plain * 1e-3), "unit": "voxel-iter/s", "ms_per_volume": ms_plain,
+                 "launches": SLICES, "note": "64 sequential single-slice solves, same kernel"}
+        pcs.pcs_destroy(ctx1)
     pcs.pcs_destroy(ctx)
 
     if rank == 0:
@@ -319,6 +341,8 @@ def run_native(args):
                     "h2d_bytes_per_step": int(pb.field.nbytes + pb.mask.nbytes),
                     "d2h_bytes_per_step": int(pb.field.nbytes)},
             "gpu_launches": args.steps,
+            "batched_vs_plain": None if plain is None else {"plain_per_slice_loop": plain,
+                                                             "speedup": plain["ms_per_volume"] / ms_step},
             "clocks": clocks,
             "wall_s_timed_region": t_wall,
             "L": L,
@@ -347,6 +371,9 @@ def main():
     ap.add_argument("--kernel", type=int, default=0, help="0 default, 1 streaming, 2 resident")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
+    ap.add_argument("--plain-loop", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the plain per-slice GPU loop (one timed volume)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

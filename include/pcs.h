@@ -70,7 +70,9 @@ typedef struct pcs_options {
     int kernel;        /* 0 = library default; 1 = streaming (state in global memory);
                           2 = resident (state kept on chip for all iterations) */
     int threads;       /* 0 = library default; else threads per CTA of a compiled variant */
-    int reserved[3];
+    int use_graph;     /* 1 = launch each solve as a CUDA graph, captured once per distinct argument
+                          set and replayed (needs a non-NULL stream); 0 = direct launch */
+    int reserved[2];
 } pcs_options;
 
 /* Diagnostics of one slice at (chi_N, p_N, q_N), in FP64 (see pcs_slice_report doc below). */

@@ -116,14 +116,86 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
     }
 }
 
+// DFT_3: with w = exp(-2 pi i/3) (forward), X1,2 = a - (b+c)/2 -/+ i (sqrt3/2)(b - c)
+constexpr float kH3 = 0.86602540378443864676f;  // sqrt(3)/2
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& a, float2& b, float2& c) {
+    const float2 t1 = cadd(b, c);
+    const float2 t2 = make_float2(fmaf(-0.5f, t1.x, a.x), fmaf(-0.5f, t1.y, a.y));
+    const float2 t3 = cscale(mul_mi<INV>(csub(b, c)), kH3);
+    a = cadd(a, t1);
+    b = cadd(t2, t3);
+    c = csub(t2, t3);
+}
+
+// cos and sin of 2 pi m / 24, m = 0..23 (multiples of 15 degrees)
+__device__ __forceinline__ constexpr float cos24(int m) {
+    constexpr float c[6] = {1.0f, 0.96592582628906828675f, 0.86602540378443864676f,
+                            0.70710678118654752440f, 0.5f, 0.25881904510252076235f};
+    m %= 24;
+    if (m < 6) return c[m];
+    if (m == 6) return 0.0f;
+    if (m < 12) return -c[12 - m];
+    if (m < 18) return -c[m - 12];
+    if (m == 18) return 0.0f;
+    return c[24 - m];
+}
+__device__ __forceinline__ constexpr float sin24(int m) { return cos24(m + 18); }  // sin x = cos(x - 90 deg)
+
+template <int R, bool INV>
+__device__ __forceinline__ void dftR(float2 (&v)[R]);
+
+// Composite DFT of length R = P*Q (Cooley-Tukey in registers): n = Q n1 + n2,
+// k = k1 + P k2; P-point DFTs over n1, twiddles W_R^{n2 k1}, Q-point DFTs over n2.
+// R divides 24 here, so every twiddle is a multiple of 15 degrees.
+template <int P, int Q, bool INV>
+__device__ __forceinline__ void dft_composite(float2 (&v)[P * Q]) {
+    constexpr int R = P * Q;
+    static_assert(24 % R == 0, "composite radix must divide 24");
+    float2 y[Q][P];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+        float2 t[P];
+#pragma unroll
+        for (int n1 = 0; n1 < P; ++n1) t[n1] = v[Q * n1 + n2];
+        dftR<P, INV>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) {
+            const int m = (n2 * k1 * (24 / R)) % 24;  // compile-time after unrolling
+            if (m == 0) {
+                y[n2][k1] = t[k1];
+            } else {
+                y[n2][k1] = mul_const<INV>(t[k1], cos24(m), -sin24(m));
+            }
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+        float2 t[Q];
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) t[n2] = y[n2][k1];
+        dftR<Q, INV>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = t[k2];
+    }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dftR(float2 (&v)[R]) {
     if constexpr (R == 2) {
         dft2<INV>(v[0], v[1]);
+    } else if constexpr (R == 3) {
+        dft3<INV>(v[0], v[1], v[2]);
     } else if constexpr (R == 4) {
         dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 6) {
+        dft_composite<2, 3, INV>(v);
     } else if constexpr (R == 8) {
         dft8<INV>(v);
+    } else if constexpr (R == 12) {
+        dft_composite<4, 3, INV>(v);
+    } else if constexpr (R == 24) {
+        dft_composite<8, 3, INV>(v);
     } else {
         static_assert(R == 16, "radix");
         dft16<INV>(v);
@@ -142,6 +214,16 @@ template <> struct Plan<512, 16> { static constexpr int R1 = 16, RM = 16, RL = 2
 template <> struct Plan<128, 8>  { static constexpr int R1 = 8,  RM = 8,  RL = 2; };
 template <> struct Plan<256, 8>  { static constexpr int R1 = 8,  RM = 8,  RL = 4; };
 template <> struct Plan<512, 8>  { static constexpr int R1 = 8,  RM = 8,  RL = 8; };
+// lengths 3 * 2^k (slice sizes 192 and 384)
+template <> struct Plan<96, 12>  { static constexpr int R1 = 12, RM = 4,  RL = 2; };
+template <> struct Plan<192, 12> { static constexpr int R1 = 12, RM = 4,  RL = 4; };
+template <> struct Plan<384, 24> { static constexpr int R1 = 8,  RM = 8,  RL = 6; };
+
+// Elements per lane for a transform of length N: 16 for powers of two >= 128,
+// 8 below; 12 for 96 and 192; 24 for 384 (so that N / E lanes is a power of two).
+constexpr int default_elems(int N) {
+    return (N % 3 == 0) ? (N == 384 ? 24 : 12) : (N >= 128 ? 16 : 8);
+}
 
 // Per-stage twiddle tables of one transform length: the middle stage's
 // (span R1, radix RM) entries first, then the last stage's (span N/RL, radix RL).
@@ -175,7 +257,7 @@ struct StageTw {
 template <int R, int NS, bool INV>
 __device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __restrict__ stw) {
     if constexpr (NS > 1) {
-        const int k = j & (NS - 1);
+        const int k = j % NS;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
             float2 w = stw[(r - 1) * NS + k];
@@ -230,7 +312,7 @@ __device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf
             const int j = g + b * T;
             twiddle<RM, NS, INV>(v[b], j, stw);
             dftR<RM, INV>(v[b]);
-            const int k = j & (NS - 1);
+            const int k = j % NS;
             const int base = (j / NS) * NS * RM + k;
 #pragma unroll
             for (int r = 0; r < RM; ++r) buf[P(base + r * NS)] = v[b][r];

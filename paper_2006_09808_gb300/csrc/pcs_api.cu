@@ -42,8 +42,8 @@ pcs_status cuda_fail(cudaError_t e, const char* what) {
 
 std::vector<pcs::KernelEntry> all_entries() {
     std::vector<pcs::KernelEntry> v;
-    const pcs::KernelEntry* (*fns[])(int*) = {pcs::entries_64, pcs::entries_128, pcs::entries_256,
-                                               pcs::entries_512};
+    const pcs::KernelEntry* (*fns[])(int*) = {pcs::entries_64,  pcs::entries_128, pcs::entries_192,
+                                               pcs::entries_256, pcs::entries_384, pcs::entries_512};
     for (auto fn : fns) {
         int n = 0;
         const pcs::KernelEntry* e = fn(&n);
@@ -148,6 +148,11 @@ struct pcs_ctx {
     double* Ldev = nullptr;
     float* xa = nullptr;
     float* xb = nullptr;
+    // CUDA-graph replay (use_graph): the last captured solve and its arguments
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    pcs::PDParams graph_prm{};
+    int graph_ncl = 0;
     std::mutex mu;
 };
 
@@ -159,6 +164,8 @@ void free_ctx(pcs_ctx* c) {
                     c->st_field, c->st_mask, c->st_chi, c->partials, c->Ldev, c->xa, c->xb};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     delete c;
 }
 
@@ -185,6 +192,7 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out))
         return fail(PCS_EINVAL, "device buffers must be 16-byte aligned");
     pcs::PDParams prm;
+    std::memset(&prm, 0, sizeof(prm));  // padding too: the graph cache compares whole structs
     prm.field = field;
     prm.mask = mask;
     prm.chi = chi_out;
@@ -205,7 +213,33 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     if (ncl > S) ncl = S;
     if (ncl < 1) ncl = 1;
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    PCS_CUDA(ctx->entry->launch(prm, ncl, ctx->stream), "launch of the primal-dual kernel");
+    if (ctx->opt.use_graph) {
+        // replay the captured graph when the arguments are those it was captured with
+        const bool same = ctx->graph_exec && ncl == ctx->graph_ncl &&
+                          std::memcmp(&prm, &ctx->graph_prm, sizeof(prm)) == 0;
+        if (!same) {
+            if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+            if (ctx->graph) cudaGraphDestroy(ctx->graph);
+            ctx->graph_exec = nullptr;
+            ctx->graph = nullptr;
+            PCS_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+            cudaError_t le = ctx->entry->launch(prm, ncl, ctx->stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+            if (le != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(le, "launch during graph capture");
+            }
+            PCS_CUDA(ce, "graph capture end");
+            ctx->graph = g;
+            PCS_CUDA(cudaGraphInstantiate(&ctx->graph_exec, g, 0), "graph instantiate");
+            ctx->graph_prm = prm;
+            ctx->graph_ncl = ncl;
+        }
+        PCS_CUDA(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
+    } else {
+        PCS_CUDA(ctx->entry->launch(prm, ncl, ctx->stream), "launch of the primal-dual kernel");
+    }
     ctx->last_iters = n_iter;
     return PCS_OK;
 }
@@ -320,6 +354,8 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
     if (opt) o = *opt;
     if (o.b0_axis != 0 && o.b0_axis != 1) return fail(PCS_EINVAL, "b0_axis must be 0 or 1");
     if (o.kernel < 0 || o.kernel > 2) return fail(PCS_EINVAL, "kernel must be 0, 1 or 2");
+    if (o.use_graph && cuda_stream == nullptr)
+        return fail(PCS_EINVAL, "use_graph needs a non-NULL stream (the legacy stream cannot be captured)");
     const pcs::KernelEntry* entry = find_entry(H, W, o.cluster_size, o.kernel, o.threads);
     if (!entry)
         return fail(PCS_EUNSUPPORTED, "no kernel for %d x %d slices with cluster_size %d, kernel %d, threads %d", H,
@@ -371,6 +407,7 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
 
 pcs_status pcs_set_stream(pcs_ctx* ctx, void* cuda_stream) {
     if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
+    if (ctx->opt.use_graph && cuda_stream == nullptr) return fail(PCS_EINVAL, "use_graph needs a non-NULL stream");
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     return PCS_OK;
 }

@@ -71,8 +71,8 @@ pcs_status err(pcs_status st, const char* what, cudaError_t e) {
 }
 
 const pcs::KernelEntry* default_entry(int H, int W) {
-    const pcs::KernelEntry* (*fns[])(int*) = {pcs::entries_64, pcs::entries_128, pcs::entries_256,
-                                               pcs::entries_512};
+    const pcs::KernelEntry* (*fns[])(int*) = {pcs::entries_64,  pcs::entries_128, pcs::entries_192,
+                                               pcs::entries_256, pcs::entries_384, pcs::entries_512};
     for (auto fn : fns) {
         int n = 0;
         const pcs::KernelEntry* e = fn(&n);

@@ -76,10 +76,10 @@ struct Geo {
     static constexpr int MC = M / C;   // spectrum columns per CTA
     static constexpr int NTW = (H > W) ? H : W;
     // row transforms (length M)
-    static constexpr int ER = ER_ ? ER_ : ((M >= 128) ? 16 : 8);
+    static constexpr int ER = ER_ ? ER_ : default_elems(M);
     static constexpr int TR = M / ER;
     // column transforms (length H)
-    static constexpr int EC = EC_ ? EC_ : ((H >= 128) ? 16 : 8);
+    static constexpr int EC = EC_ ? EC_ : default_elems(H);
     static constexpr int TC = H / EC;
     static constexpr int NW = NT / 32;
     static constexpr int RPP = NW * (32 / TR);  // rows in flight per CTA
@@ -100,6 +100,7 @@ struct Geo {
     static constexpr int CPASSES = (MC >= CPP) ? MC / CPP : 1;  // groups beyond MC idle
     static_assert(MC % TR == 0, "gather/scatter owner is compile-time per element");
     static_assert(W % 4 == 0 && H % 16 == 0, "shape");
+    static_assert((TR & (TR - 1)) == 0 && (TC & (TC - 1)) == 0, "lane groups tile a warp");
 };
 
 template <int T>
@@ -186,7 +187,7 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __res
 #pragma unroll
             for (int e = 0; e < EC; ++e) {
                 const int ky = g + TC * e;
-                const float2 ym = col[P((H - ky) & (H - 1))];
+                const float2 ym = col[P((H - ky) % H)];
                 const float dm = __ldg(dtab + ky), dd = __ldg(ddtab + ky);
                 x[e] = make_float2(fmaf(dm, x[e].x, dd * ym.x), fmaf(dm, x[e].y, -dd * ym.y));
             }

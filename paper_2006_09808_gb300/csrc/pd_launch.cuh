@@ -127,7 +127,9 @@ constexpr KernelEntry make_resident_entry() {
 // Per-size translation units define these (pd_<size>.cu).
 const KernelEntry* entries_64(int* n);
 const KernelEntry* entries_128(int* n);
+const KernelEntry* entries_192(int* n);
 const KernelEntry* entries_256(int* n);
+const KernelEntry* entries_384(int* n);
 const KernelEntry* entries_512(int* n);
 
 }  // namespace pcs

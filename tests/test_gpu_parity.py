@@ -175,6 +175,45 @@ def test_parity_512():
         assert rel_l2(got[s], ref[s]) <= TOL, s
 
 
+@pytest.mark.parametrize("H,S,n_iter", [(192, 3, 120), (384, 2, 60)])
+def test_parity_radix3_sizes(H, S, n_iter):
+    pb = phantoms.volume(H, H, S, seed=H, lam=5e-4, n_iter=n_iter)
+    L, tau, sigma = steps(H, H)
+    ref = oracle_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter)
+    got = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter)
+    for s in range(S):
+        assert rel_l2(got[s], ref[s]) <= TOL, s
+
+
+def test_graph_replay_matches_direct_launch():
+    pb = phantoms.volume(128, 128, 4, seed=41, lam=1e-3, n_iter=60)
+    L, tau, sigma = steps(128, 128)
+    direct = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter)
+    stream = torch.cuda.Stream()
+    f = torch.from_numpy(pb.field).cuda()
+    m = torch.from_numpy(pb.mask).cuda()
+    chi = torch.empty_like(f)
+    ctx = pcs.pcs_create(128, 128, 4, use_graph=True, stream=stream)
+    try:
+        for n_iter in (pb.n_iter, pb.n_iter, 7, pb.n_iter):  # replay, re-capture, re-capture
+            with torch.cuda.stream(stream):
+                chi.fill_(float("nan"))
+                pcs.pcs_solve_slices(ctx, f, m, pb.lam, tau, sigma, n_iter, chi)
+            stream.synchronize()
+            if n_iter == pb.n_iter:
+                assert np.array_equal(chi.cpu().numpy(), direct)
+    finally:
+        pcs.pcs_destroy(ctx)
+    with pytest.raises(pcs.PcsError) as ei:  # the legacy stream cannot be captured
+        lib = pcs.load_library()
+        opt = pcs.pcs_options()
+        lib.pcs_options_default(opt)
+        opt.use_graph = 1
+        h = __import__("ctypes").c_void_p()
+        pcs._check(lib.pcs_create(h, 128, 128, 1, opt, None), "pcs_create")
+    assert ei.value.status == pcs.PCS_EINVAL
+
+
 def test_b0_along_columns():
     pb = phantoms.volume(64, 64, 2, seed=8, lam=1.0, n_iter=120)
     L, _, _ = steps(64, 64, b0_axis=1)
