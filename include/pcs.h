@@ -162,6 +162,57 @@ PCS_API pcs_status pcs_report(pcs_ctx *ctx, const float *field, const unsigned c
 PCS_API pcs_status pcs_opnorm(pcs_ctx *ctx, const unsigned char *mask, int S, int power_iters,
                       double *L_out);
 
+/* ---------------------------------------------------------------- uneven batches */
+
+typedef struct pcs_batch pcs_batch; /* opaque */
+
+/* One volume of a batch: S slices of H x W, its own lambda; device buffers, caller-owned. */
+typedef struct pcs_volume {
+    int H, W, S, pad;
+    double lambda;
+    const float *field;        /* device [S][H][W] */
+    const unsigned char *mask; /* device [S][H][W] */
+    float *chi_out;            /* device [S][H][W] */
+} pcs_volume;
+
+/* What the autotuner chose for one slice size, and what it measured. */
+typedef struct pcs_tuning {
+    int H, W;
+    int cluster_size, kernel, threads; /* the chosen variant (kernel: 1 streaming, 2 resident) */
+    int n_candidates;
+    double L;                          /* ||K||_2 of the full-mask operator; tau = sigma = 1/L */
+    double ns_per_voxel_iter[8];       /* trial time of each candidate, in registry order */
+    int cand_cluster_size[8], cand_kernel[8], cand_threads[8];
+} pcs_tuning;
+
+/*
+ * Create a batch solver: all slices of all volumes of a call are solved by the
+ * fused primal-dual kernels -- one persistent launch per slice size, the
+ * launches of the different sizes forked onto their own streams and joined
+ * back into cuda_stream.  Step sizes are tau = sigma = 1/L(H, W), L the norm
+ * of the full-mask operator K (Sec. II.A pseudocode step 1), computed once per
+ * size on the GPU.  autotune != 0: the first solve of a new slice size times
+ * every compiled kernel variant of that size on that call's slice count
+ * (a short trial) and keeps the fastest; otherwise the library default (or
+ * the variant opt selects) is used.
+ */
+PCS_API pcs_status pcs_batch_create(pcs_batch **out, const pcs_options *opt, int autotune, void *cuda_stream);
+
+/*
+ * Solve every slice of every volume with n_iter iterations of the Sec. II.A
+ * iteration (each volume with its own lambda) and write each volume's chi_out.
+ * Enqueued on the batch stream; inputs are copied into per-size packed
+ * buffers owned by the batch.  Errors: PCS_EINVAL, PCS_EUNSUPPORTED, PCS_ENOMEM,
+ * PCS_ECUDA.
+ */
+PCS_API pcs_status pcs_batch_solve(pcs_batch *b, const pcs_volume *vols, int n_vols, int n_iter);
+
+/* The tuning record of slice size H x W (PCS_EINVAL if that size was never solved). */
+PCS_API pcs_status pcs_batch_tuning(pcs_batch *b, int H, int W, pcs_tuning *out);
+
+/* Release the batch solver. NULL-safe. */
+PCS_API void pcs_batch_destroy(pcs_batch *b);
+
 /*
  * Solve without allocating device memory (the paper has no counterpart; this
  * is a deployment aid).  For callers that may not call cudaMalloc once they

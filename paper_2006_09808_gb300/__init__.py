@@ -55,6 +55,47 @@ class pcs_slice_report(ctypes.Structure):
         return {k: getattr(self, k) for k in ("objective", "gap", "stationarity", "data_residual", "iters")}
 
 
+class pcs_volume(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("S", ctypes.c_int),
+        ("pad", ctypes.c_int),
+        ("lam", ctypes.c_double),
+        ("field", ctypes.c_void_p),
+        ("mask", ctypes.c_void_p),
+        ("chi_out", ctypes.c_void_p),
+    ]
+
+
+class pcs_tuning(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("cluster_size", ctypes.c_int),
+        ("kernel", ctypes.c_int),
+        ("threads", ctypes.c_int),
+        ("n_candidates", ctypes.c_int),
+        ("L", ctypes.c_double),
+        ("ns_per_voxel_iter", ctypes.c_double * 8),
+        ("cand_cluster_size", ctypes.c_int * 8),
+        ("cand_kernel", ctypes.c_int * 8),
+        ("cand_threads", ctypes.c_int * 8),
+    ]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {
+            "H": self.H, "W": self.W, "cluster_size": self.cluster_size, "kernel": self.kernel,
+            "threads": self.threads, "L": self.L,
+            "candidates": [
+                {"cluster_size": self.cand_cluster_size[k], "kernel": self.cand_kernel[k],
+                 "threads": self.cand_threads[k], "ns_per_voxel_iter": self.ns_per_voxel_iter[k]}
+                for k in range(n)
+            ],
+        }
+
+
 _lib = None
 
 
@@ -81,6 +122,10 @@ def load_library(path: str = LIB_PATH):
         "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
         "pcs_solve_slices_noalloc": (i, [vp, vp, i, i, i, d, d, d, i, vp, i, vp]),
         "pcs_destroy": (None, [vp]),
+        "pcs_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(pcs_options), i, vp]),
+        "pcs_batch_solve": (i, [vp, ctypes.POINTER(pcs_volume), i, i]),
+        "pcs_batch_tuning": (i, [vp, i, i, ctypes.POINTER(pcs_tuning)]),
+        "pcs_batch_destroy": (None, [vp]),
         "pcs_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -225,6 +270,45 @@ def pcs_solve_slices_noalloc(field, mask, lam: float, tau: float, sigma: float, 
 def pcs_destroy(ctx):
     if ctx is not None:
         load_library().pcs_destroy(ctx)
+
+
+def pcs_batch_create(autotune: bool = True, stream=None, **opts):
+    """Create an uneven-batch solver (see include/pcs.h); opts as for pcs_create."""
+    import torch
+
+    lib = load_library()
+    opt = pcs_options()
+    lib.pcs_options_default(ctypes.byref(opt))
+    for k, v in opts.items():
+        setattr(opt, k, int(v))
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    h = ctypes.c_void_p()
+    _check(lib.pcs_batch_create(ctypes.byref(h), ctypes.byref(opt), 1 if autotune else 0, ctypes.c_void_p(s)),
+           "pcs_batch_create")
+    return h
+
+
+def pcs_batch_solve(batch, volumes, n_iter: int):
+    """volumes: list of (field, mask, lam, chi_out) with [S][H][W] CUDA tensors."""
+    arr = (pcs_volume * max(1, len(volumes)))()
+    for k, (field, mask, lam, chi) in enumerate(volumes):
+        S, H, W = field.shape
+        arr[k].H, arr[k].W, arr[k].S, arr[k].lam = H, W, S, lam
+        arr[k].field = _dev_ptr(field, "float32", (S, H, W), "field").value
+        arr[k].mask = _dev_ptr(mask, "uint8", (S, H, W), "mask").value
+        arr[k].chi_out = _dev_ptr(chi, "float32", (S, H, W), "chi_out").value
+    _check(load_library().pcs_batch_solve(batch, arr, len(volumes), n_iter), "pcs_batch_solve")
+
+
+def pcs_batch_tuning(batch, H: int, W: int):
+    t = pcs_tuning()
+    _check(load_library().pcs_batch_tuning(batch, H, W, ctypes.byref(t)), "pcs_batch_tuning")
+    return t.as_dict()
+
+
+def pcs_batch_destroy(batch):
+    if batch is not None:
+        load_library().pcs_batch_destroy(batch)
 
 
 class Solver:

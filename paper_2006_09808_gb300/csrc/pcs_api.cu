@@ -188,7 +188,8 @@ pcs_status validate_solve(pcs_ctx* ctx, const void* field, const void* mask, int
 }
 
 pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
-                        double tau, double sigma, int n_iter, float* chi_out) {
+                        double tau, double sigma, int n_iter, float* chi_out,
+                        const float* inv_den_slice = nullptr) {
     if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out))
         return fail(PCS_EINVAL, "device buffers must be 16-byte aligned");
     pcs::PDParams prm;
@@ -208,6 +209,7 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     prm.sigma = (float)sigma;
     prm.tau = (float)tau;
     prm.inv_den = (float)(1.0 / (1.0 + sigma / lambda));
+    prm.inv_den_slice = inv_den_slice;
     int ncl = ctx->max_clusters;
     if (ctx->opt.max_clusters > 0 && ctx->opt.max_clusters < ncl) ncl = ctx->opt.max_clusters;
     if (ncl > S) ncl = S;
@@ -472,5 +474,274 @@ pcs_status pcs_opnorm(pcs_ctx* ctx, const unsigned char* mask, int S, int power_
 void pcs_destroy(pcs_ctx* ctx) { free_ctx(ctx); }
 
 const char* pcs_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ uneven batches
+
+struct pcs_batch {
+    struct Class {
+        int H = 0, W = 0;
+        pcs_ctx* ctx = nullptr;  // holds the chosen variant; max_slices = capacity
+        double L = 0.0;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t done = nullptr;
+        float* pk_field = nullptr;  // packed inputs / outputs [capacity][H][W]
+        unsigned char* pk_mask = nullptr;
+        float* pk_chi = nullptr;
+        float* inv_den = nullptr;  // [capacity]
+        int capacity = 0;
+        pcs_tuning tuning{};
+        bool tuned = false;
+    };
+    pcs_options opt{};
+    int autotune = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    cudaEvent_t fork = nullptr;
+    std::vector<Class> classes;
+    std::mutex mu;
+};
+
+namespace {
+
+void free_class(pcs_batch::Class& c) {
+    if (c.ctx) pcs_destroy(c.ctx);
+    void* ptrs[] = {c.pk_field, c.pk_mask, c.pk_chi, c.inv_den};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (c.stream) cudaStreamDestroy(c.stream);
+    if (c.done) cudaEventDestroy(c.done);
+    c = pcs_batch::Class();
+}
+
+// Time every compiled variant of H x W on S zero-field slices (trial_iters
+// iterations each, after one untimed run) and record them in c.tuning.
+pcs_status tune_class(pcs_batch* b, pcs_batch::Class& c, int S, int trial_iters) {
+    const size_t n = (size_t)S * c.H * c.W;
+    float *f = nullptr, *chi = nullptr;
+    unsigned char* m = nullptr;
+    PCS_CUDA(cudaMalloc(&f, n * sizeof(float)), "cudaMalloc tuning");
+    PCS_CUDA(cudaMalloc(&chi, n * sizeof(float)), "cudaMalloc tuning");
+    PCS_CUDA(cudaMalloc(&m, n), "cudaMalloc tuning");
+    PCS_CUDA(cudaMemsetAsync(f, 0, n * sizeof(float), c.stream), "memset");
+    PCS_CUDA(cudaMemsetAsync(m, 1, n, c.stream), "memset");
+    cudaEvent_t e0, e1;
+    PCS_CUDA(cudaEventCreate(&e0), "event");
+    PCS_CUDA(cudaEventCreate(&e1), "event");
+    pcs_tuning& t = c.tuning;
+    t = pcs_tuning{};
+    t.H = c.H;
+    t.W = c.W;
+    double best = 1e300;
+    pcs_status st = PCS_OK;
+    for (const auto& e : entries()) {
+        if (e.H != c.H || e.W != c.W || t.n_candidates >= 8) continue;
+        pcs_options o = b->opt;
+        o.cluster_size = e.C;
+        o.kernel = e.resident ? 2 : 1;
+        o.threads = e.threads;
+        o.use_graph = 0;
+        pcs_ctx* tc = nullptr;
+        st = pcs_create(&tc, c.H, c.W, S, &o, c.stream);
+        if (st != PCS_OK) break;
+        float ms = 0.f;
+        st = launch_solve(tc, f, m, S, 1.0, 0.35, 0.35, 2, chi);  // untimed warm-up
+        if (st == PCS_OK) {
+            cudaEventRecord(e0, c.stream);
+            st = launch_solve(tc, f, m, S, 1.0, 0.35, 0.35, trial_iters, chi);
+            cudaEventRecord(e1, c.stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        pcs_destroy(tc);
+        if (st != PCS_OK) break;
+        const int k = t.n_candidates++;
+        t.ns_per_voxel_iter[k] = 1e6 * ms / ((double)n * trial_iters);
+        t.cand_cluster_size[k] = e.C;
+        t.cand_kernel[k] = e.resident ? 2 : 1;
+        t.cand_threads[k] = e.threads;
+        if (t.ns_per_voxel_iter[k] < best) {
+            best = t.ns_per_voxel_iter[k];
+            t.cluster_size = e.C;
+            t.kernel = e.resident ? 2 : 1;
+            t.threads = e.threads;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(f);
+    cudaFree(chi);
+    cudaFree(m);
+    if (st != PCS_OK) return st;
+    c.tuned = true;
+    return PCS_OK;
+}
+
+// Make class c ready for S slices: variant chosen, context and packed buffers
+// large enough, L known.
+pcs_status prepare_class(pcs_batch* b, pcs_batch::Class& c, int S) {
+    if (!c.stream) {
+        PCS_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        PCS_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (b->autotune && !c.tuned) {
+        pcs_status st = tune_class(b, c, S < 128 ? S : 128, 40);
+        if (st != PCS_OK) return st;
+    }
+    if (c.ctx && c.capacity >= S) return PCS_OK;
+    const int cap = S > 2 * c.capacity ? S : 2 * c.capacity;
+    if (c.ctx) pcs_destroy(c.ctx);
+    c.ctx = nullptr;
+    void* old[] = {c.pk_field, c.pk_mask, c.pk_chi, c.inv_den};
+    for (void* q : old)
+        if (q) cudaFree(q);
+    c.pk_field = nullptr;
+    c.pk_mask = nullptr;
+    c.pk_chi = nullptr;
+    c.inv_den = nullptr;
+    pcs_options o = b->opt;
+    o.use_graph = 0;
+    if (c.tuned) {
+        o.cluster_size = c.tuning.cluster_size;
+        o.kernel = c.tuning.kernel;
+        o.threads = c.tuning.threads;
+    }
+    pcs_status st = pcs_create(&c.ctx, c.H, c.W, cap, &o, c.stream);
+    if (st != PCS_OK) return st;
+    const size_t n = (size_t)cap * c.H * c.W;
+    PCS_CUDA(cudaMalloc(&c.pk_field, n * sizeof(float)), "cudaMalloc batch");
+    PCS_CUDA(cudaMalloc(&c.pk_mask, n), "cudaMalloc batch");
+    PCS_CUDA(cudaMalloc(&c.pk_chi, n * sizeof(float)), "cudaMalloc batch");
+    PCS_CUDA(cudaMalloc(&c.inv_den, (size_t)cap * sizeof(float)), "cudaMalloc batch");
+    c.capacity = cap;
+    if (c.L == 0.0) {  // full-mask operator norm of this size (pseudocode step 1)
+        PCS_CUDA(cudaMemsetAsync(c.pk_mask, 1, (size_t)c.H * c.W, c.stream), "memset");
+        st = pcs::ctx_opnorm(c.ctx, c.pk_mask, 1, 300, &c.L);
+        if (st != PCS_OK) return st;
+    }
+    return PCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcs_status pcs_batch_create(pcs_batch** out, const pcs_options* opt, int autotune, void* cuda_stream) {
+    if (!out) return fail(PCS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) return fail(PCS_ECUDA, "no CUDA device (%s)", cudaGetErrorString(e));
+    pcs_batch* b = new pcs_batch();
+    if (opt) b->opt = *opt;
+    b->autotune = autotune;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if ((e = cudaGetDevice(&b->device)) != cudaSuccess || (e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "batch set-up");
+    }
+    *out = b;
+    return PCS_OK;
+}
+
+pcs_status pcs_batch_solve(pcs_batch* b, const pcs_volume* vols, int n_vols, int n_iter) {
+    if (!b) return fail(PCS_EINVAL, "batch is NULL");
+    if (n_vols < 0 || (n_vols > 0 && !vols)) return fail(PCS_EINVAL, "bad volume list");
+    if (n_iter < 0) return fail(PCS_EINVAL, "n_iter must be >= 0");
+    std::unique_lock<std::mutex> lk(b->mu, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(PCS_EBUSY, "batch in use by another thread");
+    // validate and group by slice size
+    std::vector<int> cls_of(n_vols, -1);
+    std::vector<int> cls_S;
+    for (int v = 0; v < n_vols; ++v) {
+        const pcs_volume& V = vols[v];
+        if (V.S < 0) return fail(PCS_EINVAL, "volume %d: S < 0", v);
+        if (V.S == 0) continue;
+        if (!V.field || !V.mask || !V.chi_out) return fail(PCS_EINVAL, "volume %d: NULL buffer", v);
+        if (!(V.lambda > 0.0) || !std::isfinite(V.lambda)) return fail(PCS_EINVAL, "volume %d: lambda must be > 0", v);
+        if (!find_entry(V.H, V.W, 0)) return fail(PCS_EUNSUPPORTED, "volume %d: no kernel for %d x %d", v, V.H, V.W);
+        int k = -1;
+        for (size_t c = 0; c < b->classes.size(); ++c)
+            if (b->classes[c].H == V.H && b->classes[c].W == V.W) k = (int)c;
+        if (k < 0) {
+            b->classes.emplace_back();
+            b->classes.back().H = V.H;
+            b->classes.back().W = V.W;
+            k = (int)b->classes.size() - 1;
+        }
+        cls_of[v] = k;
+        if ((int)cls_S.size() < (int)b->classes.size()) cls_S.resize(b->classes.size(), 0);
+        cls_S[k] += V.S;
+    }
+    cls_S.resize(b->classes.size(), 0);
+    PCS_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        if (cls_S[c] == 0) continue;
+        pcs_status st = prepare_class(b, b->classes[c], cls_S[c]);
+        if (st != PCS_OK) return st;
+    }
+    // fork: every class stream waits for the work already on the batch stream
+    PCS_CUDA(cudaEventRecord(b->fork, b->stream), "fork record");
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        if (cls_S[c] == 0) continue;
+        pcs_batch::Class& C = b->classes[c];
+        PCS_CUDA(cudaStreamWaitEvent(C.stream, b->fork, 0), "fork wait");
+        const size_t sl = (size_t)C.H * C.W;
+        const double tau = 1.0 / C.L, sigma = 1.0 / C.L;
+        std::vector<float> inv(cls_S[c]);
+        int off = 0;
+        for (int v = 0; v < n_vols; ++v) {
+            if (cls_of[v] != (int)c) continue;
+            const pcs_volume& V = vols[v];
+            PCS_CUDA(cudaMemcpyAsync(C.pk_field + off * sl, V.field, V.S * sl * sizeof(float), cudaMemcpyDeviceToDevice, C.stream), "pack field");
+            PCS_CUDA(cudaMemcpyAsync(C.pk_mask + off * sl, V.mask, V.S * sl, cudaMemcpyDeviceToDevice, C.stream), "pack mask");
+            for (int s = 0; s < V.S; ++s) inv[off + s] = (float)(1.0 / (1.0 + sigma / V.lambda));
+            off += V.S;
+        }
+        PCS_CUDA(cudaMemcpyAsync(C.inv_den, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice, C.stream), "lambda upload");
+        pcs_status st = launch_solve(C.ctx, C.pk_field, C.pk_mask, cls_S[c], 1.0, tau, sigma, n_iter, C.pk_chi, C.inv_den);
+        if (st != PCS_OK) return st;
+        off = 0;
+        for (int v = 0; v < n_vols; ++v) {
+            if (cls_of[v] != (int)c) continue;
+            const pcs_volume& V = vols[v];
+            PCS_CUDA(cudaMemcpyAsync(V.chi_out, C.pk_chi + off * sl, V.S * sl * sizeof(float), cudaMemcpyDeviceToDevice, C.stream), "unpack chi");
+            off += V.S;
+        }
+        PCS_CUDA(cudaEventRecord(C.done, C.stream), "join record");
+        PCS_CUDA(cudaStreamWaitEvent(b->stream, C.done, 0), "join wait");
+    }
+    return PCS_OK;
+}
+
+pcs_status pcs_batch_tuning(pcs_batch* b, int H, int W, pcs_tuning* out) {
+    if (!b || !out) return fail(PCS_EINVAL, "NULL argument");
+    for (const auto& c : b->classes)
+        if (c.H == H && c.W == W) {
+            if (!c.tuned) {
+                const pcs::KernelEntry* e = c.ctx ? c.ctx->entry : find_entry(H, W, 0);
+                *out = pcs_tuning{};
+                out->H = H;
+                out->W = W;
+                out->cluster_size = e ? e->C : 0;
+                out->kernel = e ? (e->resident ? 2 : 1) : 0;
+                out->threads = e ? e->threads : 0;
+                out->L = c.L;
+                return PCS_OK;
+            }
+            *out = c.tuning;
+            out->L = c.L;
+            return PCS_OK;
+        }
+    return fail(PCS_EINVAL, "size %d x %d not solved by this batch", H, W);
+}
+
+void pcs_batch_destroy(pcs_batch* b) {
+    if (!b) return;
+    for (auto& c : b->classes) free_class(c);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
 
 }  // extern "C"

@@ -176,6 +176,7 @@ extern "C" pcs_status pcs_solve_slices_noalloc(const float* field, const unsigne
     prm.sigma = (float)sigma;
     prm.tau = (float)tau;
     prm.inv_den = (float)(1.0 / (1.0 + sigma / lambda));
+    prm.inv_den_slice = nullptr;
     int ncl = d.max_clusters[slot];
     if (ncl > S) ncl = S;
     if (ncl < 1) ncl = 1;

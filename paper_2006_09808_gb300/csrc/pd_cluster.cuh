@@ -59,8 +59,13 @@ struct PDParams {
     int n_iter;
     float sigma;
     float tau;
-    float inv_den;  // 1 / (1 + sigma / lambda)
+    float inv_den;               // 1 / (1 + sigma / lambda)
+    const float* inv_den_slice;  // NULL, or per-slice 1 / (1 + sigma / lambda_s) [S]
 };
+
+__device__ __forceinline__ float slice_inv_den(const PDParams& prm, int s) {
+    return prm.inv_den_slice ? __ldg(prm.inv_den_slice + s) : prm.inv_den;
+}
 
 constexpr int ceil_to_mod16(int v, int want) {  // smallest x >= v with x % 16 == want % 16
     return v + ((want % 16) - (v % 16) + 16) % 16;
@@ -283,7 +288,7 @@ constexpr int kChunk = 4;
 // q and p stay exactly zero wherever the 0/1 mask is zero (zero start, masked
 // increments), so W p = p and M q = q: the adjoint transform takes p as is.
 template <class G>
-__device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm, size_t base) {
+__device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm, size_t base, float inv_den) {
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
     constexpr int CH = (ER < kChunk) ? ER : kChunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -292,7 +297,7 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm
     const unsigned gm = group_mask<TR>(lane);
     const int src_right = (g == TR - 1) ? lane - (TR - 1) : lane + 1;  // lane holding pixel 2n+2
     float2* rs = cx.rows + grp * G::MP;
-    const float sigma = prm.sigma, inv_den = prm.inv_den;
+    const float sigma = prm.sigma;
     const float* __restrict__ fld = prm.field;
     const unsigned char* __restrict__ msk = prm.mask;
     const float* __restrict__ cbar = prm.chibar;
@@ -441,6 +446,7 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParams prm
 #pragma unroll 1
     for (int s = cid; s < prm.S; s += ncl) {
         const size_t base = (size_t)s * SLICE;
+        const float inv_den = slice_inv_den(prm, s);
         // zero start (pseudocode steps 2-3): chi, chibar, p, q of own rows, own spectrum
         {
             const size_t o = base + (size_t)cx.crank * OWN;
@@ -460,7 +466,7 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParams prm
                 column_pass<G>(cx, prm.dtab, prm.ddtab);  // u-spectrum = D F chibar_n
                 cluster_barrier<G::C>();
             }
-            phase_dual<G>(cx, prm, base);
+            phase_dual<G>(cx, prm, base, inv_den);
             cluster_barrier<G::C>();
             column_pass<G>(cx, prm.dtab, prm.ddtab);  // v-spectrum = D F (W p_{n+1})
             cluster_barrier<G::C>();

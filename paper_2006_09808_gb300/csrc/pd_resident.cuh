@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(G::NT, 1) pd_resident_kernel(PDParams prm) {
     const int il = grp;
     const int i = cx.crank * R + il;
     const bool has_up = (i > 0), has_down = (i + 1 < H);
-    const float sigma = prm.sigma, tau = prm.tau, inv_den = prm.inv_den;
+    const float sigma = prm.sigma, tau = prm.tau;
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
     constexpr size_t SLICE = (size_t)H * W;
 
@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(G::NT, 1) pd_resident_kernel(PDParams prm) {
     for (int s = cid; s < prm.S; s += ncl) {
         const size_t base = (size_t)s * SLICE;
         const size_t rowoff = base + (size_t)i * W;
+        const float inv_den = slice_inv_den(prm, s);
         // ---- zero start; field and mask of own rows into shared memory
         float2 chi[ER], pv[ER];
 #pragma unroll
