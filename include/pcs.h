@@ -162,6 +162,18 @@ PCS_API pcs_status pcs_report(pcs_ctx *ctx, const float *field, const unsigned c
 PCS_API pcs_status pcs_opnorm(pcs_ctx *ctx, const unsigned char *mask, int S, int power_iters,
                       double *L_out);
 
+/*
+ * All-FP64 solve (precision study): the same fused iteration kernel
+ * instantiated with double state, double transforms and double D(k) /
+ * twiddle tables (computed in FP64, not rounded).  field and chi_out are
+ * device double [S][H][W], mask uint8; tau, sigma, lambda as for
+ * pcs_solve_slices.  Allocates and frees its own scratch and synchronises
+ * the stream before returning.  Compiled sizes: 64 x 64 and 256 x 256 (others: PCS_EUNSUPPORTED).
+ */
+PCS_API pcs_status pcs_solve_slices_f64(const double *field, const unsigned char *mask, int H, int W, int S,
+                                        double lambda, double tau, double sigma, int n_iter, double *chi_out,
+                                        int b0_axis, void *cuda_stream);
+
 /* ---------------------------------------------------------------- uneven batches */
 
 typedef struct pcs_batch pcs_batch; /* opaque */

@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
         "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
         "pcs_solve_slices_noalloc": (i, [vp, vp, i, i, i, d, d, d, i, vp, i, vp]),
         "pcs_destroy": (None, [vp]),
+        "pcs_solve_slices_f64": (i, [vp, vp, i, i, i, d, d, d, i, vp, i, vp]),
         "pcs_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(pcs_options), i, vp]),
         "pcs_batch_solve": (i, [vp, ctypes.POINTER(pcs_volume), i, i]),
         "pcs_batch_tuning": (i, [vp, i, i, ctypes.POINTER(pcs_tuning)]),
@@ -270,6 +271,20 @@ def pcs_solve_slices_noalloc(field, mask, lam: float, tau: float, sigma: float, 
 def pcs_destroy(ctx):
     if ctx is not None:
         load_library().pcs_destroy(ctx)
+
+
+def pcs_solve_slices_f64(field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, b0_axis: int = 0,
+                         stream=None):
+    """All-FP64 solve of field/mask (float64 / uint8 CUDA tensors [S][H][W]) into chi_out (float64)."""
+    import torch
+
+    S, H, W = field.shape
+    f = _dev_ptr(field, "float64", (S, H, W), "field")
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    c = _dev_ptr(chi_out, "float64", (S, H, W), "chi_out")
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(load_library().pcs_solve_slices_f64(f, m, H, W, S, lam, tau, sigma, n_iter, c, b0_axis,
+                                               ctypes.c_void_p(s)), "pcs_solve_slices_f64")
 
 
 def pcs_batch_create(autotune: bool = True, stream=None, **opts):

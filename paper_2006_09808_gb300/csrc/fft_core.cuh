@@ -28,43 +28,62 @@ namespace pcs {
 
 __device__ __forceinline__ int P(int i) { return i + (i >> 4); }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+// Complex vector type of a real type: float -> float2, double -> double2.
+template <class Real>
+struct Cplx;
+template <>
+struct Cplx<float> {
+    using T = float2;
+};
+template <>
+struct Cplx<double> {
+    using T = double2;
+};
+template <class V>
+using RealOf = decltype(V::x);
+
+template <class V>
+__device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <class V>
+__device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <class V>
+__device__ __forceinline__ V cmul(V a, V b) {
+    return V{fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)};
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+template <class V>
+__device__ __forceinline__ V cscale(V a, RealOf<V> s) { return V{a.x * s, a.y * s}; }
+template <class V>
+__device__ __forceinline__ V conjf2(V a) { return V{a.x, -a.y}; }
 
 // multiply by -i (forward) or +i (inverse)
-template <bool INV>
-__device__ __forceinline__ float2 mul_mi(float2 a) {
-    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+template <bool INV, class V>
+__device__ __forceinline__ V mul_mi(V a) {
+    return INV ? V{-a.y, a.x} : V{a.y, -a.x};
 }
 
 // multiply by the constant (c, s) with s given for the forward sign; INV flips it
-template <bool INV>
-__device__ __forceinline__ float2 mul_const(float2 a, float c, float s) {
-    const float ss = INV ? -s : s;
-    return make_float2(fmaf(a.x, c, -a.y * ss), fmaf(a.x, ss, a.y * c));
+template <bool INV, class V>
+__device__ __forceinline__ V mul_const(V a, RealOf<V> c, RealOf<V> s) {
+    const RealOf<V> ss = INV ? -s : s;
+    return V{fma(a.x, c, -a.y * ss), fma(a.x, ss, a.y * c)};
 }
 
-// cos / sin of 2*pi*k/16 (forward twiddles are (cos, -sin))
-constexpr float kC1 = 0.92387953251128675613f;  // cos(pi/8)
-constexpr float kS1 = 0.38268343236508977173f;  // sin(pi/8)
-constexpr float kR2 = 0.70710678118654752440f;  // sqrt(1/2)
+// cos / sin of 2*pi*k/16 (forward twiddles are (cos, -sin)), rounded once to the real type
+constexpr double kC1 = 0.92387953251128675613;  // cos(pi/8)
+constexpr double kS1 = 0.38268343236508977173;  // sin(pi/8)
+constexpr double kR2 = 0.70710678118654752440;  // sqrt(1/2)
 
-template <bool INV>
-__device__ __forceinline__ void dft2(float2& a, float2& b) {
-    const float2 t = a;
+template <bool INV, class V>
+__device__ __forceinline__ void dft2(V& a, V& b) {
+    const V t = a;
     a = cadd(t, b);
     b = csub(t, b);
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
-    const float2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
-    const float2 t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
+template <bool INV, class V>
+__device__ __forceinline__ void dft4(V& v0, V& v1, V& v2, V& v3) {
+    const V t0 = cadd(v0, v2), t1 = csub(v0, v2);
+    const V t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
     v0 = cadd(t0, t2);
     v2 = csub(t0, t2);
     v1 = cadd(t1, t3);
@@ -72,15 +91,16 @@ __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2&
 }
 
 // in-place, natural order in and out
-template <bool INV>
-__device__ __forceinline__ void dft8(float2 (&v)[8]) {
-    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+template <bool INV, class V>
+__device__ __forceinline__ void dft8(V (&v)[8]) {
+    using Rl = RealOf<V>;
+    V e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    V o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
     dft4<INV>(e0, e1, e2, e3);
     dft4<INV>(o0, o1, o2, o3);
-    o1 = mul_const<INV>(o1, kR2, -kR2);
+    o1 = mul_const<INV>(o1, Rl(kR2), Rl(-kR2));
     o2 = mul_mi<INV>(o2);
-    o3 = mul_const<INV>(o3, -kR2, -kR2);
+    o3 = mul_const<INV>(o3, Rl(-kR2), Rl(-kR2));
     v[0] = cadd(e0, o0);
     v[4] = csub(e0, o0);
     v[1] = cadd(e1, o1);
@@ -91,9 +111,10 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
     v[7] = csub(e3, o3);
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft16(float2 (&v)[16]) {
-    float2 e[8], o[8];
+template <bool INV, class V>
+__device__ __forceinline__ void dft16(V (&v)[16]) {
+    using Rl = RealOf<V>;
+    V e[8], o[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         e[t] = v[2 * t];
@@ -102,13 +123,13 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
     dft8<INV>(e);
     dft8<INV>(o);
     // W16^k = (cos(2 pi k/16), -sin(2 pi k/16)) forward
-    o[1] = mul_const<INV>(o[1], kC1, -kS1);
-    o[2] = mul_const<INV>(o[2], kR2, -kR2);
-    o[3] = mul_const<INV>(o[3], kS1, -kC1);
+    o[1] = mul_const<INV>(o[1], Rl(kC1), Rl(-kS1));
+    o[2] = mul_const<INV>(o[2], Rl(kR2), Rl(-kR2));
+    o[3] = mul_const<INV>(o[3], Rl(kS1), Rl(-kC1));
     o[4] = mul_mi<INV>(o[4]);
-    o[5] = mul_const<INV>(o[5], -kS1, -kC1);
-    o[6] = mul_const<INV>(o[6], -kR2, -kR2);
-    o[7] = mul_const<INV>(o[7], -kC1, -kS1);
+    o[5] = mul_const<INV>(o[5], Rl(-kS1), Rl(-kC1));
+    o[6] = mul_const<INV>(o[6], Rl(-kR2), Rl(-kR2));
+    o[7] = mul_const<INV>(o[7], Rl(-kC1), Rl(-kS1));
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         v[t] = cadd(e[t], o[t]);
@@ -117,45 +138,47 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 }
 
 // DFT_3: with w = exp(-2 pi i/3) (forward), X1,2 = a - (b+c)/2 -/+ i (sqrt3/2)(b - c)
-constexpr float kH3 = 0.86602540378443864676f;  // sqrt(3)/2
-template <bool INV>
-__device__ __forceinline__ void dft3(float2& a, float2& b, float2& c) {
-    const float2 t1 = cadd(b, c);
-    const float2 t2 = make_float2(fmaf(-0.5f, t1.x, a.x), fmaf(-0.5f, t1.y, a.y));
-    const float2 t3 = cscale(mul_mi<INV>(csub(b, c)), kH3);
+constexpr double kH3 = 0.86602540378443864676;  // sqrt(3)/2
+template <bool INV, class V>
+__device__ __forceinline__ void dft3(V& a, V& b, V& c) {
+    using Rl = RealOf<V>;
+    const V t1 = cadd(b, c);
+    const V t2 = V{fma(Rl(-0.5), t1.x, a.x), fma(Rl(-0.5), t1.y, a.y)};
+    const V t3 = cscale(mul_mi<INV>(csub(b, c)), Rl(kH3));
     a = cadd(a, t1);
     b = cadd(t2, t3);
     c = csub(t2, t3);
 }
 
 // cos and sin of 2 pi m / 24, m = 0..23 (multiples of 15 degrees)
-__device__ __forceinline__ constexpr float cos24(int m) {
-    constexpr float c[6] = {1.0f, 0.96592582628906828675f, 0.86602540378443864676f,
-                            0.70710678118654752440f, 0.5f, 0.25881904510252076235f};
+__device__ __forceinline__ constexpr double cos24(int m) {
+    constexpr double c[6] = {1.0, 0.96592582628906828675, 0.86602540378443864676,
+                             0.70710678118654752440, 0.5, 0.25881904510252076235};
     m %= 24;
     if (m < 6) return c[m];
-    if (m == 6) return 0.0f;
+    if (m == 6) return 0.0;
     if (m < 12) return -c[12 - m];
     if (m < 18) return -c[m - 12];
-    if (m == 18) return 0.0f;
+    if (m == 18) return 0.0;
     return c[24 - m];
 }
-__device__ __forceinline__ constexpr float sin24(int m) { return cos24(m + 18); }  // sin x = cos(x - 90 deg)
+__device__ __forceinline__ constexpr double sin24(int m) { return cos24(m + 18); }  // sin x = cos(x - 90 deg)
 
-template <int R, bool INV>
-__device__ __forceinline__ void dftR(float2 (&v)[R]);
+template <int R, bool INV, class V>
+__device__ __forceinline__ void dftR(V (&v)[R]);
 
 // Composite DFT of length R = P*Q (Cooley-Tukey in registers): n = Q n1 + n2,
 // k = k1 + P k2; P-point DFTs over n1, twiddles W_R^{n2 k1}, Q-point DFTs over n2.
 // R divides 24 here, so every twiddle is a multiple of 15 degrees.
-template <int P, int Q, bool INV>
-__device__ __forceinline__ void dft_composite(float2 (&v)[P * Q]) {
+template <int P, int Q, bool INV, class V>
+__device__ __forceinline__ void dft_composite(V (&v)[P * Q]) {
+    using Rl = RealOf<V>;
     constexpr int R = P * Q;
     static_assert(24 % R == 0, "composite radix must divide 24");
-    float2 y[Q][P];
+    V y[Q][P];
 #pragma unroll
     for (int n2 = 0; n2 < Q; ++n2) {
-        float2 t[P];
+        V t[P];
 #pragma unroll
         for (int n1 = 0; n1 < P; ++n1) t[n1] = v[Q * n1 + n2];
         dftR<P, INV>(t);
@@ -165,13 +188,13 @@ __device__ __forceinline__ void dft_composite(float2 (&v)[P * Q]) {
             if (m == 0) {
                 y[n2][k1] = t[k1];
             } else {
-                y[n2][k1] = mul_const<INV>(t[k1], cos24(m), -sin24(m));
+                y[n2][k1] = mul_const<INV>(t[k1], Rl(cos24(m)), Rl(-sin24(m)));
             }
         }
     }
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) {
-        float2 t[Q];
+        V t[Q];
 #pragma unroll
         for (int n2 = 0; n2 < Q; ++n2) t[n2] = y[n2][k1];
         dftR<Q, INV>(t);
@@ -180,8 +203,8 @@ __device__ __forceinline__ void dft_composite(float2 (&v)[P * Q]) {
     }
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void dftR(float2 (&v)[R]) {
+template <int R, bool INV, class V>
+__device__ __forceinline__ void dftR(V (&v)[R]) {
     if constexpr (R == 2) {
         dft2<INV>(v[0], v[1]);
     } else if constexpr (R == 3) {
@@ -189,13 +212,13 @@ __device__ __forceinline__ void dftR(float2 (&v)[R]) {
     } else if constexpr (R == 4) {
         dft4<INV>(v[0], v[1], v[2], v[3]);
     } else if constexpr (R == 6) {
-        dft_composite<2, 3, INV>(v);
+        dft_composite<2, 3, INV, V>(v);
     } else if constexpr (R == 8) {
         dft8<INV>(v);
     } else if constexpr (R == 12) {
-        dft_composite<4, 3, INV>(v);
+        dft_composite<4, 3, INV, V>(v);
     } else if constexpr (R == 24) {
-        dft_composite<8, 3, INV>(v);
+        dft_composite<8, 3, INV, V>(v);
     } else {
         static_assert(R == 16, "radix");
         dft16<INV>(v);
@@ -234,7 +257,8 @@ struct StageTw {
     static constexpr int LAST = (PL::RL - 1) * (N / PL::RL);
     static constexpr int SIZE = MID + LAST;
     // dst[(r-1) NS + k] = W_{NS R}^{r k} = tw[r k (N / (NS R)) TWS], TWS = NTW / N
-    __device__ static void fill(float2* dst, const float2* __restrict__ tw, int TWS, int tid, int nthr) {
+    template <class V>
+    __device__ static void fill(V* dst, const V* __restrict__ tw, int TWS, int tid, int nthr) {
         if constexpr (MID > 0) {
             constexpr int NS = PL::R1, R = PL::RM, STEP = N / (NS * R);
             for (int t = tid; t < MID; t += nthr) {
@@ -254,13 +278,13 @@ struct StageTw {
 
 // Twiddle the legs of one butterfly of a stage with span NS and radix R
 // (stw: that stage's [r-1][k] table).
-template <int R, int NS, bool INV>
-__device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __restrict__ stw) {
+template <int R, int NS, bool INV, class V>
+__device__ __forceinline__ void twiddle(V (&v)[R], int j, const V* __restrict__ stw) {
     if constexpr (NS > 1) {
         const int k = j % NS;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-            float2 w = stw[(r - 1) * NS + k];
+            V w = stw[(r - 1) * NS + k];
             if (INV) w.y = -w.y;
             v[r] = cmul(v[r], w);
         }
@@ -270,9 +294,9 @@ __device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __r
 // Complex FFT of length N by a group of T lanes (lane g, group mask gm).
 // x: E = N/T elements, element g + T*e in x[e]; buf: group-private padded
 // buffer of P(N-1)+1 entries (contents destroyed); stw: StageTw<N, E> table.
-template <int N, int T, bool INV>
-__device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf,
-                                    const float2* __restrict__ stw, int g, unsigned gm) {
+template <int N, int T, bool INV, class V>
+__device__ __forceinline__ void fft(V (&x)[N / T], V* __restrict__ buf, const V* __restrict__ stw, int g,
+                                    unsigned gm) {
     constexpr int E = N / T;
     using PL = Plan<N, E>;
     constexpr int R1 = PL::R1, RM = PL::RM, RL = PL::RL;
@@ -285,10 +309,10 @@ __device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf
         constexpr int B = E / R1;
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            float2 v[R1];
+            V v[R1];
 #pragma unroll
             for (int r = 0; r < R1; ++r) v[r] = x[b + r * B];
-            dftR<R1, INV>(v);
+            dftR<R1, INV, V>(v);
             const int j = g + b * T;
 #pragma unroll
             for (int r = 0; r < R1; ++r) buf[P(j * R1 + r)] = v[r];
@@ -299,7 +323,7 @@ __device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf
     if constexpr (RM != 0) {
         constexpr int B = E / RM;
         constexpr int NS = R1;
-        float2 v[B][RM];
+        V v[B][RM];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int j = g + b * T;
@@ -310,8 +334,8 @@ __device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int j = g + b * T;
-            twiddle<RM, NS, INV>(v[b], j, stw);
-            dftR<RM, INV>(v[b]);
+            twiddle<RM, NS, INV, V>(v[b], j, stw);
+            dftR<RM, INV, V>(v[b]);
             const int k = j % NS;
             const int base = (j / NS) * NS * RM + k;
 #pragma unroll
@@ -326,11 +350,11 @@ __device__ __forceinline__ void fft(float2 (&x)[N / T], float2* __restrict__ buf
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int j = g + b * T;
-            float2 v[RL];
+            V v[RL];
 #pragma unroll
             for (int r = 0; r < RL; ++r) v[r] = buf[P(j + r * NS)];
-            twiddle<RL, NS, INV>(v, j, stw + StageTw<N, E>::MID);
-            dftR<RL, INV>(v);
+            twiddle<RL, NS, INV, V>(v, j, stw + StageTw<N, E>::MID);
+            dftR<RL, INV, V>(v);
 #pragma unroll
             for (int r = 0; r < RL; ++r) x[b + r * B] = v[r];
         }

@@ -83,7 +83,8 @@ namespace pcs {
 // entry divided by H*W (the unnormalised transforms' scale).  Column kx = 0
 // holds Dm = (D(ky,0) + D(ky,W/2))/2 and ddtab[ky] = (D(ky,0) - D(ky,W/2))/2,
 // the two halves of the packed DC/Nyquist column.
-void build_dipole_tables(int H, int W, int b0_axis, std::vector<float>& dtab, std::vector<float>& ddtab) {
+template <class T>
+void build_dipole_tables_t(int H, int W, int b0_axis, std::vector<T>& dtab, std::vector<T>& ddtab) {
     const int M = W / 2;
     auto freq = [](int idx, int n) {  // cycles per pixel, numpy.fft.fftfreq convention
         return (idx < (n + 1) / 2) ? (double)idx / n : (double)(idx - n) / n;
@@ -96,26 +97,32 @@ void build_dipole_tables(int H, int W, int b0_axis, std::vector<float>& dtab, st
         return 1.0 / 3.0 - kp * kp / k2;
     };
     const double scale = 1.0 / ((double)H * (double)W);
-    dtab.assign((size_t)M * H, 0.f);
-    ddtab.assign((size_t)H, 0.f);
+    dtab.assign((size_t)M * H, T(0));
+    ddtab.assign((size_t)H, T(0));
     for (int kx = 0; kx < M; ++kx)
-        for (int ky = 0; ky < H; ++ky) dtab[(size_t)kx * H + ky] = (float)(D(ky, kx) * scale);
+        for (int ky = 0; ky < H; ++ky) dtab[(size_t)kx * H + ky] = (T)(D(ky, kx) * scale);
     for (int ky = 0; ky < H; ++ky) {
         const double d0 = D(ky, 0), d1 = D(ky, M);
-        dtab[ky] = (float)(0.5 * (d0 + d1) * scale);
-        ddtab[ky] = (float)(0.5 * (d0 - d1) * scale);
+        dtab[ky] = (T)(0.5 * (d0 + d1) * scale);
+        ddtab[ky] = (T)(0.5 * (d0 - d1) * scale);
     }
+}
+void build_dipole_tables(int H, int W, int b0_axis, std::vector<float>& dtab, std::vector<float>& ddtab) {
+    build_dipole_tables_t<float>(H, W, b0_axis, dtab, ddtab);
 }
 
 // tw[m] = exp(-2 pi i m / n), m in [0, n)
-void build_twiddles(int n, std::vector<float2>& tw) {
+template <class V>
+void build_twiddles_t(int n, std::vector<V>& tw) {
     tw.resize(n);
     const double two_pi = 6.283185307179586476925286766559;
     for (int m = 0; m < n; ++m) {
         const double a = two_pi * (double)m / (double)n;
-        tw[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+        tw[m].x = (decltype(tw[m].x))std::cos(a);
+        tw[m].y = (decltype(tw[m].y))-std::sin(a);
     }
 }
+void build_twiddles(int n, std::vector<float2>& tw) { build_twiddles_t<float2>(n, tw); }
 
 }  // namespace pcs
 
@@ -745,3 +752,71 @@ void pcs_batch_destroy(pcs_batch* b) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ all-FP64 solve (precision study)
+
+extern "C" pcs_status pcs_solve_slices_f64(const double* field, const unsigned char* mask, int H, int W, int S,
+                                           double lambda, double tau, double sigma, int n_iter, double* chi_out,
+                                           int b0_axis, void* cuda_stream) {
+    if (S < 0 || n_iter < 0) return fail(PCS_EINVAL, "S and n_iter must be >= 0");
+    const pcs::KernelEntryF64* entry = nullptr;
+    int ne = 0;
+    const pcs::KernelEntryF64* es = pcs::entries_f64(&ne);
+    for (int k = 0; k < ne; ++k)
+        if (es[k].H == H && es[k].W == W) entry = &es[k];
+    if (!entry) return fail(PCS_EUNSUPPORTED, "no FP64 kernel for %d x %d slices", H, W);
+    if (S == 0) return PCS_OK;
+    if (!field || !mask || !chi_out || (const void*)field == (const void*)chi_out)
+        return fail(PCS_EINVAL, "NULL or aliased buffer");
+    if (!(lambda > 0.0) || !(tau > 0.0) || !(sigma > 0.0)) return fail(PCS_EINVAL, "lambda, tau, sigma must be > 0");
+    if (b0_axis != 0 && b0_axis != 1) return fail(PCS_EINVAL, "b0_axis must be 0 or 1");
+    if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out)) return fail(PCS_EINVAL, "16-byte alignment");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<double> dtab, ddtab;
+    std::vector<double2> tw;
+    pcs::build_dipole_tables_t<double>(H, W, b0_axis, dtab, ddtab);
+    pcs::build_twiddles_t<double2>(H > W ? H : W, tw);
+    const size_t n = (size_t)S * H * W;
+    double* scratch = nullptr;
+    const size_t tab = dtab.size() + ddtab.size() + 2 * tw.size();
+    PCS_CUDA(cudaMalloc(&scratch, (4 * n + tab) * sizeof(double)), "cudaMalloc FP64 scratch");
+    double* dt = scratch + 4 * n;
+    double* ddt = dt + dtab.size();
+    double2* twd = reinterpret_cast<double2*>(ddt + ddtab.size());
+    pcs_status ret = PCS_OK;
+    cudaError_t e;
+    int ncl = 0;
+    if ((e = cudaMemcpyAsync(dt, dtab.data(), dtab.size() * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(ddt, ddtab.data(), ddtab.size() * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(twd, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = entry->prepare(&ncl)) != cudaSuccess) {
+        ret = cuda_fail(e, "FP64 set-up");
+    } else {
+        pcs::PDParamsT<double> prm;
+        std::memset(&prm, 0, sizeof(prm));
+        prm.field = field;
+        prm.mask = mask;
+        prm.chi = chi_out;
+        prm.chibar = scratch;
+        prm.p = scratch + n;
+        prm.qx = scratch + 2 * n;
+        prm.qy = scratch + 3 * n;
+        prm.dtab = dt;
+        prm.ddtab = ddt;
+        prm.twid = twd;
+        prm.S = S;
+        prm.n_iter = n_iter;
+        prm.sigma = sigma;
+        prm.tau = tau;
+        prm.inv_den = 1.0 / (1.0 + sigma / lambda);
+        prm.inv_den_slice = nullptr;
+        if (ncl > S) ncl = S;
+        if (ncl < 1) ncl = 1;
+        if ((e = entry->launch(prm, ncl, st)) != cudaSuccess) ret = cuda_fail(e, "FP64 kernel launch");
+    }
+    // the call is synchronous: it owns its scratch
+    e = cudaStreamSynchronize(st);
+    if (ret == PCS_OK && e != cudaSuccess) ret = cuda_fail(e, "stream sync");
+    cudaFree(scratch);
+    return ret;
+}

@@ -44,27 +44,36 @@ namespace pcs {
 
 namespace cg = cooperative_groups;
 
-struct PDParams {
-    const float* field;         // [S][H][W]
+template <class Real>
+struct PDParamsT {
+    using V = typename Cplx<Real>::T;
+    const Real* field;          // [S][H][W]
     const unsigned char* mask;  // [S][H][W]
-    float* chi;                 // [S][H][W]  (caller's chi_out)
-    float* chibar;              // [S][H][W]  scratch
-    float* p;                   // [S][H][W]  scratch
-    float* qx;                  // [S][H][W]  scratch
-    float* qy;                  // [S][H][W]  scratch
-    const float* dtab;          // [W/2][H]: D(ky,kx)/(HW), column kx=0 holds Dm
-    const float* ddtab;         // [H]: Dd for the packed column
-    const float2* twid;         // [NTW]: exp(-2 pi i m / NTW)
+    Real* chi;                  // [S][H][W]  (caller's chi_out)
+    Real* chibar;               // [S][H][W]  scratch
+    Real* p;                    // [S][H][W]  scratch
+    Real* qx;                   // [S][H][W]  scratch
+    Real* qy;                   // [S][H][W]  scratch
+    const Real* dtab;           // [W/2][H]: D(ky,kx)/(HW), column kx=0 holds Dm
+    const Real* ddtab;          // [H]: Dd for the packed column
+    const V* twid;              // [NTW]: exp(-2 pi i m / NTW)
     int S;
     int n_iter;
-    float sigma;
-    float tau;
-    float inv_den;               // 1 / (1 + sigma / lambda)
-    const float* inv_den_slice;  // NULL, or per-slice 1 / (1 + sigma / lambda_s) [S]
+    Real sigma;
+    Real tau;
+    Real inv_den;               // 1 / (1 + sigma / lambda)
+    const Real* inv_den_slice;  // NULL, or per-slice 1 / (1 + sigma / lambda_s) [S]
 };
+using PDParams = PDParamsT<float>;
 
-__device__ __forceinline__ float slice_inv_den(const PDParams& prm, int s) {
+template <class Real>
+__device__ __forceinline__ Real slice_inv_den(const PDParamsT<Real>& prm, int s) {
     return prm.inv_den_slice ? __ldg(prm.inv_den_slice + s) : prm.inv_den;
+}
+
+template <class V>
+__device__ __forceinline__ V mk(RealOf<V> a, RealOf<V> b) {
+    return V{a, b};
 }
 
 constexpr int ceil_to_mod16(int v, int want) {  // smallest x >= v with x % 16 == want % 16
@@ -73,8 +82,10 @@ constexpr int ceil_to_mod16(int v, int want) {  // smallest x >= v with x % 16 =
 
 // ER_, EC_: elements per lane of the row / column transforms (0 = 16 for
 // lengths >= 128, else 8).
-template <int H_, int W_, int C_, int MINB_ = 1, int NT_ = 256, int ER_ = 0, int EC_ = 0>
+template <int H_, int W_, int C_, int MINB_ = 1, int NT_ = 256, int ER_ = 0, int EC_ = 0, class Real_ = float>
 struct Geo {
+    using Real = Real_;                       // arithmetic type of state and transforms
+    using V = typename Cplx<Real>::T;         // its complex vector type
     static constexpr int H = H_, W = W_, C = C_, NT = NT_, MINB = MINB_;
     static constexpr int M = W / 2;    // complex row length (packed half spectrum)
     static constexpr int R = H / C;    // rows per CTA
@@ -89,7 +100,7 @@ struct Geo {
     static constexpr int NW = NT / 32;
     static constexpr int RPP = NW * (32 / TR);  // rows in flight per CTA
     static constexpr int CPP = NW * (32 / TC);  // columns in flight per CTA
-    // shared-memory layout (float2 units)
+    // shared-memory layout (complex units)
     static constexpr int HP = H + H / 16 + 1;                        // column stride (odd)
     static constexpr int MP = ceil_to_mod16(M + M / 16, TR % 16);    // row-scratch stride
     static constexpr int SM_TBUF = MC * HP;
@@ -97,7 +108,7 @@ struct Geo {
     static constexpr int SM_TW = NTW;
     static constexpr int SM_STW_R = StageTw<M, ER>::SIZE;  // row-transform stage twiddles
     static constexpr int SM_STW_C = StageTw<H, EC>::SIZE;  // column-transform stage twiddles
-    static constexpr size_t SMEM_BYTES = sizeof(float2) * (SM_TBUF + SM_ROWS + SM_TW + SM_STW_R + SM_STW_C);
+    static constexpr size_t SMEM_BYTES = sizeof(V) * (SM_TBUF + SM_ROWS + SM_TW + SM_STW_R + SM_STW_C);
 
     static_assert(TR <= 32 && TC <= 32, "group fits a warp");
     static_assert(R % RPP == 0, "row passes");
@@ -128,19 +139,22 @@ __device__ __forceinline__ void cluster_barrier() {
 
 template <class G>
 struct Ctx {
-    float2* tbuf;     // own spectrum columns, [MC][HP]
-    float2* rows;     // row scratch, [RPP][MP]
-    float2* tw;       // twiddles [NTW]
-    float2* stw_r;    // stage twiddles of the row transforms
-    float2* stw_c;    // stage twiddles of the column transforms
-    float2* tb[G::C]; // spectrum columns of every CTA of the cluster (DSMEM)
+    using V = typename G::V;
+    V* tbuf;     // own spectrum columns, [MC][HP]
+    V* rows;     // row scratch, [RPP][MP]
+    V* tw;       // twiddles [NTW]
+    V* stw_r;    // stage twiddles of the row transforms
+    V* stw_c;    // stage twiddles of the column transforms
+    V* tb[G::C]; // spectrum columns of every CTA of the cluster (DSMEM)
     int crank;
 };
 
 // Carve the shared-memory layout and load the twiddle tables (no barrier).
 template <class G>
-__device__ __forceinline__ void ctx_init(Ctx<G>& cx, unsigned char* smem_raw, const float2* __restrict__ twid) {
-    cx.tbuf = reinterpret_cast<float2*>(smem_raw);
+__device__ __forceinline__ void ctx_init(Ctx<G>& cx, unsigned char* smem_raw, const typename G::V* __restrict__ twid) {
+    using V = typename G::V;
+    using Real = typename G::Real;
+    cx.tbuf = reinterpret_cast<V*>(smem_raw);
     cx.rows = cx.tbuf + G::SM_TBUF;
     cx.tw = cx.rows + G::SM_ROWS;
     cx.stw_r = cx.tw + G::SM_TW;
@@ -163,8 +177,10 @@ __device__ __forceinline__ void ctx_init(Ctx<G>& cx, unsigned char* smem_raw, co
 // Forward column FFT, multiply by D/(HW), inverse column FFT, in place on the
 // CTA's own spectrum columns.
 template <class G>
-__device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __restrict__ dtab,
-                                            const float* __restrict__ ddtab) {
+__device__ __forceinline__ void column_pass(const Ctx<G>& cx, const typename G::Real* __restrict__ dtab,
+                                            const typename G::Real* __restrict__ ddtab) {
+    using V = typename G::V;
+    using Real = typename G::Real;
     constexpr int H = G::H, TC = G::TC, EC = G::EC;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % TC;
@@ -175,13 +191,13 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __res
         const int cl = pass * G::CPP + grp;
         if (G::CPP > G::MC && cl >= G::MC) break;  // whole group idles (uniform per group)
         const int kx = cx.crank * G::MC + cl;
-        float2* col = cx.tbuf + cl * G::HP;
-        float2 x[EC];
+        V* col = cx.tbuf + cl * G::HP;
+        V x[EC];
 #pragma unroll
         for (int e = 0; e < EC; ++e) x[e] = col[P(g + TC * e)];
         fft<H, TC, false>(x, col, cx.stw_c, g, gm);
         if (kx != 0) {
-            const float* d = dtab + (size_t)kx * H;
+            const Real* d = dtab + (size_t)kx * H;
 #pragma unroll
             for (int e = 0; e < EC; ++e) x[e] = cscale(x[e], __ldg(d + g + TC * e));
         } else {
@@ -192,9 +208,9 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __res
 #pragma unroll
             for (int e = 0; e < EC; ++e) {
                 const int ky = g + TC * e;
-                const float2 ym = col[P((H - ky) % H)];
-                const float dm = __ldg(dtab + ky), dd = __ldg(ddtab + ky);
-                x[e] = make_float2(fmaf(dm, x[e].x, dd * ym.x), fmaf(dm, x[e].y, -dd * ym.y));
+                const V ym = col[P((H - ky) % H)];
+                const Real dm = __ldg(dtab + ky), dd = __ldg(ddtab + ky);
+                x[e] = mk<V>(fma(dm, x[e].x, dd * ym.x), fma(dm, x[e].y, -dd * ym.y));
             }
         }
         fft<H, TC, true>(x, col, cx.stw_c, g, gm);
@@ -209,11 +225,13 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const float* __res
 // row transform.  Result: x[e] = W * (y[2n], y[2n+1]) for n = g + TR*e, where
 // y is the real row (the D table carries 1/(HW), so x is the true D-product).
 template <class G>
-__device__ __forceinline__ void row_inverse(const Ctx<G>& cx, float2* rs, int i, int g, unsigned gm,
-                                            float2 (&x)[G::ER]) {
+__device__ __forceinline__ void row_inverse(const Ctx<G>& cx, typename G::V* rs, int i, int g, unsigned gm,
+                                            typename G::V (&x)[G::ER]) {
+    using V = typename G::V;
+    using Real = typename G::Real;
     constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
     {
-        float2 t[ER];  // all remote loads in flight before any local store
+        V t[ER];  // all remote loads in flight before any local store
 #pragma unroll
         for (int e = 0; e < ER; ++e) {
             const int k = g + TR * e;
@@ -228,17 +246,17 @@ __device__ __forceinline__ void row_inverse(const Ctx<G>& cx, float2* rs, int i,
 #pragma unroll
     for (int e = 0; e < ER; ++e) {
         const int k = g + TR * e;
-        const float2 X = rs[P(k)];
+        const V X = rs[P(k)];
         if (k == 0) {
             // X[0] = Re, X[M] = Im of the packed entry
-            x[e] = make_float2(X.x + X.y, X.x - X.y);
+            x[e] = mk<V>(X.x + X.y, X.x - X.y);
         } else {
-            const float2 Xm = rs[P(M - k)];
-            const float2 ec = make_float2(X.x + Xm.x, X.y - Xm.y);   // X + conj(Xm)
-            const float2 od0 = make_float2(X.x - Xm.x, X.y + Xm.y);  // X - conj(Xm)
-            const float2 w = cx.tw[k * (NTW / W)];                    // exp(-2 pi i k / W)
-            const float2 od = cmul(od0, conjf2(w));
-            x[e] = make_float2(ec.x - od.y, ec.y + od.x);  // ec + i od
+            const V Xm = rs[P(M - k)];
+            const V ec = mk<V>(X.x + Xm.x, X.y - Xm.y);   // X + conj(Xm)
+            const V od0 = mk<V>(X.x - Xm.x, X.y + Xm.y);  // X - conj(Xm)
+            const V w = cx.tw[k * (NTW / W)];                    // exp(-2 pi i k / W)
+            const V od = cmul(od0, conjf2(w));
+            x[e] = mk<V>(ec.x - od.y, ec.y + od.x);  // ec + i od
         }
     }
     fft<M, TR, true>(x, rs, cx.stw_r, g, gm);
@@ -247,8 +265,10 @@ __device__ __forceinline__ void row_inverse(const Ctx<G>& cx, float2* rs, int i,
 // Forward real row transform of z[e] = (x[2n], x[2n+1]), n = g + TR*e, and
 // scatter of the packed spectrum row i to the owners of its columns.
 template <class G>
-__device__ __forceinline__ void row_forward(const Ctx<G>& cx, float2* rs, int i, int g, unsigned gm,
-                                            float2 (&z)[G::ER]) {
+__device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs, int i, int g, unsigned gm,
+                                            typename G::V (&z)[G::ER]) {
+    using V = typename G::V;
+    using Real = typename G::Real;
     constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
     fft<M, TR, false>(z, rs, cx.stw_r, g, gm);
 #pragma unroll
@@ -257,17 +277,17 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, float2* rs, int i,
 #pragma unroll
     for (int e = 0; e < ER; ++e) {
         const int k = g + TR * e;
-        const float2 A = z[e];
-        float2 out;
+        const V A = z[e];
+        V out;
         if (k == 0) {
-            out = make_float2(A.x + A.y, A.x - A.y);  // X[0] + i X[M]
+            out = mk<V>(A.x + A.y, A.x - A.y);  // X[0] + i X[M]
         } else {
-            const float2 Zm = rs[P(M - k)];
+            const V Zm = rs[P(M - k)];
             // E = (A + conj(Zm))/2, O = -i (A - conj(Zm))/2, X = E + w^k O
-            const float2 E = make_float2(0.5f * (A.x + Zm.x), 0.5f * (A.y - Zm.y));
-            const float2 dlt = make_float2(A.x - Zm.x, A.y + Zm.y);
-            const float2 O = make_float2(0.5f * dlt.y, -0.5f * dlt.x);
-            const float2 w = cx.tw[k * (NTW / W)];
+            const V E = mk<V>(Real(0.5) * (A.x + Zm.x), Real(0.5) * (A.y - Zm.y));
+            const V dlt = mk<V>(A.x - Zm.x, A.y + Zm.y);
+            const V O = mk<V>(Real(0.5) * dlt.y, -Real(0.5) * dlt.x);
+            const V w = cx.tw[k * (NTW / W)];
             out = cadd(E, cmul(w, O));
         }
         const int q = (TR * e) / MC;
@@ -288,7 +308,9 @@ constexpr int kChunk = 4;
 // q and p stay exactly zero wherever the 0/1 mask is zero (zero start, masked
 // increments), so W p = p and M q = q: the adjoint transform takes p as is.
 template <class G>
-__device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm, size_t base, float inv_den) {
+__device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base, typename G::Real inv_den) {
+    using V = typename G::V;
+    using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
     constexpr int CH = (ER < kChunk) ? ER : kChunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -296,41 +318,41 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm
     const int grp = warp * (32 / TR) + lane / TR;
     const unsigned gm = group_mask<TR>(lane);
     const int src_right = (g == TR - 1) ? lane - (TR - 1) : lane + 1;  // lane holding pixel 2n+2
-    float2* rs = cx.rows + grp * G::MP;
-    const float sigma = prm.sigma;
-    const float* __restrict__ fld = prm.field;
+    V* rs = cx.rows + grp * G::MP;
+    const Real sigma = prm.sigma;
+    const Real* __restrict__ fld = prm.field;
     const unsigned char* __restrict__ msk = prm.mask;
-    const float* __restrict__ cbar = prm.chibar;
-    float* __restrict__ pp = prm.p;
-    float* __restrict__ qxp = prm.qx;
-    float* __restrict__ qyp = prm.qy;
+    const Real* __restrict__ cbar = prm.chibar;
+    Real* __restrict__ pp = prm.p;
+    Real* __restrict__ qxp = prm.qx;
+    Real* __restrict__ qyp = prm.qy;
 #pragma unroll 1
     for (int pass = 0; pass < G::R / G::RPP; ++pass) {
         const int i = cx.crank * G::R + pass * G::RPP + grp;
         const size_t rowoff = base + (size_t)i * W;
         const bool has_down = (i + 1 < H);
         // chibar of this row; its right neighbours come from the next lane by shuffle
-        float2 cb[ER];
+        V cb[ER];
 #pragma unroll
-        for (int e = 0; e < ER; ++e) cb[e] = __ldcg(reinterpret_cast<const float2*>(cbar + rowoff + 2 * (g + TR * e)));
-        float2 x[ER];
+        for (int e = 0; e < ER; ++e) cb[e] = __ldcg(reinterpret_cast<const V*>(cbar + rowoff + 2 * (g + TR * e)));
+        V x[ER];
         row_inverse<G>(cx, rs, i, g, gm, x);
-        float cr[ER];
+        Real cr[ER];
 #pragma unroll
         for (int e = 0; e < ER; ++e) cr[e] = __shfl_sync(gm, cb[e].x, src_right);
 #pragma unroll
         for (int e0 = 0; e0 < ER; e0 += CH) {
-            float2 f[CH], p[CH], cd[CH], qx[CH], qy[CH];
+            V f[CH], p[CH], cd[CH], qx[CH], qy[CH];
             uchar2 mk[CH];
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const size_t o = rowoff + 2 * (g + TR * (e0 + c));
-                f[c] = __ldg(reinterpret_cast<const float2*>(fld + o));
+                f[c] = __ldg(reinterpret_cast<const V*>(fld + o));
                 mk[c] = __ldg(reinterpret_cast<const uchar2*>(msk + o));
-                p[c] = __ldcg(reinterpret_cast<const float2*>(pp + o));
-                cd[c] = has_down ? __ldcg(reinterpret_cast<const float2*>(cbar + o + W)) : cb[e0 + c];
-                qx[c] = __ldcg(reinterpret_cast<const float2*>(qxp + o));
-                qy[c] = __ldcg(reinterpret_cast<const float2*>(qyp + o));
+                p[c] = __ldcg(reinterpret_cast<const V*>(pp + o));
+                cd[c] = has_down ? __ldcg(reinterpret_cast<const V*>(cbar + o + W)) : cb[e0 + c];
+                qx[c] = __ldcg(reinterpret_cast<const V*>(qxp + o));
+                qy[c] = __ldcg(reinterpret_cast<const V*>(qyp + o));
             }
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
@@ -338,23 +360,23 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm
                 const size_t o = rowoff + 2 * (g + TR * e);
                 // pixel 2n+2 is in the next lane at the same e, or in lane 0 at e+1; past the
                 // last column the difference is zero (Neumann)
-                float right = cr[e];
+                Real right = cr[e];
                 if (g == TR - 1) right = (e + 1 < ER) ? cr[e + 1] : cb[e].y;
-                const float m0 = mk[c].x ? 1.f : 0.f, m1 = mk[c].y ? 1.f : 0.f;
-                const float2 u = x[e];
+                const Real m0 = mk[c].x ? Real(1) : Real(0), m1 = mk[c].y ? Real(1) : Real(0);
+                const V u = x[e];
                 // dual data prox (W = mask, W dB formed on the fly)
-                float2 pn;
+                V pn;
                 pn.x = (p[c].x + sigma * (m0 * (u.x - f[c].x))) * inv_den;
                 pn.y = (p[c].y + sigma * (m1 * (u.y - f[c].y))) * inv_den;
                 // dual TV prox (forward differences of chibar, Neumann boundary)
-                float2 qxn, qyn;
-                qxn.x = fminf(1.f, fmaxf(-1.f, qx[c].x + sigma * m0 * (cb[e].y - cb[e].x)));
-                qxn.y = fminf(1.f, fmaxf(-1.f, qx[c].y + sigma * m1 * (right - cb[e].y)));
-                qyn.x = fminf(1.f, fmaxf(-1.f, qy[c].x + sigma * m0 * (cd[c].x - cb[e].x)));
-                qyn.y = fminf(1.f, fmaxf(-1.f, qy[c].y + sigma * m1 * (cd[c].y - cb[e].y)));
-                __stcg(reinterpret_cast<float2*>(pp + o), pn);
-                __stcg(reinterpret_cast<float2*>(qxp + o), qxn);
-                __stcg(reinterpret_cast<float2*>(qyp + o), qyn);
+                V qxn, qyn;
+                qxn.x = fmin(Real(1), fmax(-Real(1), qx[c].x + sigma * m0 * (cb[e].y - cb[e].x)));
+                qxn.y = fmin(Real(1), fmax(-Real(1), qx[c].y + sigma * m1 * (right - cb[e].y)));
+                qyn.x = fmin(Real(1), fmax(-Real(1), qy[c].x + sigma * m0 * (cd[c].x - cb[e].x)));
+                qyn.y = fmin(Real(1), fmax(-Real(1), qy[c].y + sigma * m1 * (cd[c].y - cb[e].y)));
+                __stcg(reinterpret_cast<V*>(pp + o), pn);
+                __stcg(reinterpret_cast<V*>(qxp + o), qxn);
+                __stcg(reinterpret_cast<V*>(qyp + o), qyn);
                 x[e] = pn;  // W p = p: input of the adjoint transform
             }
         }
@@ -365,8 +387,10 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParams& prm
 // Phase A: v = D W p -> primal step -> over-relaxation -> forward transform of chibar.
 // G^T M q = G^T q because q vanishes outside the mask (see phase_dual).
 template <class G>
-__device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParams& prm, size_t base,
+__device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base,
                                              bool last) {
+    using V = typename G::V;
+    using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
     constexpr int CH = (ER < kChunk) ? ER : kChunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -374,55 +398,55 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParams& p
     const int grp = warp * (32 / TR) + lane / TR;
     const unsigned gm = group_mask<TR>(lane);
     const int src_left = (g == 0) ? lane + (TR - 1) : lane - 1;  // lane holding pixel 2n-1
-    float2* rs = cx.rows + grp * G::MP;
-    const float tau = prm.tau;
-    const float* __restrict__ qxp = prm.qx;
-    const float* __restrict__ qyp = prm.qy;
-    float* __restrict__ chip = prm.chi;
-    float* __restrict__ cbar = prm.chibar;
+    V* rs = cx.rows + grp * G::MP;
+    const Real tau = prm.tau;
+    const Real* __restrict__ qxp = prm.qx;
+    const Real* __restrict__ qyp = prm.qy;
+    Real* __restrict__ chip = prm.chi;
+    Real* __restrict__ cbar = prm.chibar;
 #pragma unroll 1
     for (int pass = 0; pass < G::R / G::RPP; ++pass) {
         const int i = cx.crank * G::R + pass * G::RPP + grp;
         const size_t rowoff = base + (size_t)i * W;
         const bool has_up = (i > 0), has_down = (i + 1 < H);
-        float2 qx[ER];
+        V qx[ER];
 #pragma unroll
-        for (int e = 0; e < ER; ++e) qx[e] = __ldcg(reinterpret_cast<const float2*>(qxp + rowoff + 2 * (g + TR * e)));
-        float2 x[ER];
+        for (int e = 0; e < ER; ++e) qx[e] = __ldcg(reinterpret_cast<const V*>(qxp + rowoff + 2 * (g + TR * e)));
+        V x[ER];
         row_inverse<G>(cx, rs, i, g, gm, x);
-        float ql[ER];
+        Real ql[ER];
 #pragma unroll
         for (int e = 0; e < ER; ++e) ql[e] = __shfl_sync(gm, qx[e].y, src_left);
 #pragma unroll
         for (int e0 = 0; e0 < ER; e0 += CH) {
-            float2 qy[CH], qu[CH], chi[CH];
+            V qy[CH], qu[CH], chi[CH];
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const size_t o = rowoff + 2 * (g + TR * (e0 + c));
-                qy[c] = __ldcg(reinterpret_cast<const float2*>(qyp + o));
-                qu[c] = has_up ? __ldcg(reinterpret_cast<const float2*>(qyp + o - W)) : make_float2(0.f, 0.f);
-                chi[c] = __ldcg(reinterpret_cast<const float2*>(chip + o));
+                qy[c] = __ldcg(reinterpret_cast<const V*>(qyp + o));
+                qu[c] = has_up ? __ldcg(reinterpret_cast<const V*>(qyp + o - W)) : mk<V>(Real(0), Real(0));
+                chi[c] = __ldcg(reinterpret_cast<const V*>(chip + o));
             }
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const int e = e0 + c;
                 const int j0 = 2 * (g + TR * e);
                 const size_t o = rowoff + j0;
-                const float2 v = x[e];
+                const V v = x[e];
                 // G^T(a,b)[j] = a[j-1][j>0] - a[j][j<W-1] + b[i-1][i>0] - b[i][i<H-1], a = qx, b = qy
-                float al = ql[e];
-                if (g == 0) al = (e > 0) ? ql[e - 1] : 0.f;
-                const float a1r = (j0 + 2 < W) ? qx[e].y : 0.f;
-                const float b0 = has_down ? qy[c].x : 0.f;
-                const float b1 = has_down ? qy[c].y : 0.f;
-                const float d0 = (al - qx[e].x) + (qu[c].x - b0);
-                const float d1 = (qx[e].x - a1r) + (qu[c].y - b1);
-                float2 cn;
+                Real al = ql[e];
+                if (g == 0) al = (e > 0) ? ql[e - 1] : Real(0);
+                const Real a1r = (j0 + 2 < W) ? qx[e].y : Real(0);
+                const Real b0 = has_down ? qy[c].x : Real(0);
+                const Real b1 = has_down ? qy[c].y : Real(0);
+                const Real d0 = (al - qx[e].x) + (qu[c].x - b0);
+                const Real d1 = (qx[e].x - a1r) + (qu[c].y - b1);
+                V cn;
                 cn.x = chi[c].x - tau * v.x - tau * d0;
                 cn.y = chi[c].y - tau * v.y - tau * d1;
-                __stcg(reinterpret_cast<float2*>(chip + o), cn);
-                const float2 cb = make_float2(2.f * cn.x - chi[c].x, 2.f * cn.y - chi[c].y);
-                if (!last) __stcg(reinterpret_cast<float2*>(cbar + o), cb);
+                __stcg(reinterpret_cast<V*>(chip + o), cn);
+                const V cb = mk<V>(Real(2) * cn.x - chi[c].x, Real(2) * cn.y - chi[c].y);
+                if (!last) __stcg(reinterpret_cast<V*>(cbar + o), cb);
                 x[e] = cb;
             }
         }
@@ -433,7 +457,9 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParams& p
 // ------------------------------------------------------------------ kernel
 
 template <class G>
-__global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParams prm) {
+__global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParamsT<typename G::Real> prm) {
+    using V = typename G::V;
+    using Real = typename G::Real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Ctx<G> cx;
     ctx_init<G>(cx, smem_raw, prm.twid);
@@ -446,18 +472,18 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParams prm
 #pragma unroll 1
     for (int s = cid; s < prm.S; s += ncl) {
         const size_t base = (size_t)s * SLICE;
-        const float inv_den = slice_inv_den(prm, s);
+        const Real inv_den = slice_inv_den(prm, s);
         // zero start (pseudocode steps 2-3): chi, chibar, p, q of own rows, own spectrum
         {
             const size_t o = base + (size_t)cx.crank * OWN;
-            float4* ptrs[5] = {reinterpret_cast<float4*>(prm.chi + o), reinterpret_cast<float4*>(prm.chibar + o),
-                               reinterpret_cast<float4*>(prm.p + o), reinterpret_cast<float4*>(prm.qx + o),
-                               reinterpret_cast<float4*>(prm.qy + o)};
-            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            V* ptrs[5] = {reinterpret_cast<V*>(prm.chi + o), reinterpret_cast<V*>(prm.chibar + o),
+                          reinterpret_cast<V*>(prm.p + o), reinterpret_cast<V*>(prm.qx + o),
+                          reinterpret_cast<V*>(prm.qy + o)};
+            const V z2 = mk<V>(Real(0), Real(0));
 #pragma unroll
             for (int a = 0; a < 5; ++a)
-                for (int t = threadIdx.x; t < OWN / 4; t += G::NT) __stcg(ptrs[a] + t, z4);
-            for (int t = threadIdx.x; t < G::SM_TBUF; t += G::NT) cx.tbuf[t] = make_float2(0.f, 0.f);
+                for (int t = threadIdx.x; t < OWN / 2; t += G::NT) __stcg(ptrs[a] + t, z2);
+            for (int t = threadIdx.x; t < G::SM_TBUF; t += G::NT) cx.tbuf[t] = mk<V>(Real(0), Real(0));
         }
         cluster_barrier<G::C>();
 #pragma unroll 1

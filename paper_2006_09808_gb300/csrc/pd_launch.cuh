@@ -124,6 +124,27 @@ constexpr KernelEntry make_resident_entry() {
                        &launch_res<GR>, &launch_report<G>, &launch_opnorm<G>};
 }
 
+// FP64 variant (precision study): iteration kernel only.
+struct KernelEntryF64 {
+    int H, W, C;
+    size_t smem;
+    cudaError_t (*prepare)(int* max_clusters);
+    cudaError_t (*launch)(const PDParamsT<double>& prm, int n_clusters, cudaStream_t stream);
+};
+template <class G>
+cudaError_t launch_pd64(const PDParamsT<double>& prm, int n_clusters, cudaStream_t stream) {
+    return launch_cluster<G>(pd_cluster_kernel<G>, prm, G::SMEM_BYTES, n_clusters, stream);
+}
+template <class G>
+cudaError_t prepare_pd64(int* max_clusters) {
+    return prepare_cluster<G>(pd_cluster_kernel<G>, G::SMEM_BYTES, max_clusters);
+}
+template <class G>
+constexpr KernelEntryF64 make_f64_entry() {
+    return KernelEntryF64{G::H, G::W, G::C, G::SMEM_BYTES, &prepare_pd64<G>, &launch_pd64<G>};
+}
+const KernelEntryF64* entries_f64(int* n);
+
 // Per-size translation units define these (pd_<size>.cu).
 const KernelEntry* entries_64(int* n);
 const KernelEntry* entries_128(int* n);
