@@ -225,6 +225,68 @@ PCS_API pcs_status pcs_batch_tuning(pcs_batch *b, int H, int W, pcs_tuning *out)
 /* Release the batch solver. NULL-safe. */
 PCS_API void pcs_batch_destroy(pcs_batch *b);
 
+/* ---------------------------------------------------------------- serving loop */
+
+typedef struct pcs_server pcs_server; /* opaque */
+
+typedef struct pcs_server_config {
+    size_t hbm_budget_bytes; /* device memory the admitted requests may hold (25 B per voxel) */
+    int slots;               /* requests in flight at once (one CUDA stream each) */
+    int n_iter;              /* primal-dual iterations per slice */
+    int autotune;            /* pick each slice size's kernel variant by timing (see pcs_batch_create) */
+    int b0_axis;             /* as in pcs_options */
+    int reserved[4];
+} pcs_server_config;
+
+typedef struct pcs_serve_summary {
+    long long completed;     /* requests finished */
+    long long pending;       /* requests open or running */
+    double voxel_iters;      /* sum over finished requests of S*H*W*n_iter */
+    double span_s;           /* first open -> last completion */
+    double p50_s, p99_s, max_s; /* per-volume latency (open -> last slice back on the host) */
+    double peak_bytes;       /* peak budget in use */
+    int peak_inflight, pad;
+} pcs_serve_summary;
+
+/*
+ * Start a server: a scheduler thread that admits volume requests by arrival
+ * order, slot and memory budget, solves each request's slices as they arrive
+ * (chunks of different requests run concurrently on their slots' streams;
+ * a request's primal/dual state stays on the device until it completes),
+ * and copies chi back into the request's host buffer.  Slices are solved
+ * independently, so a volume's chi does not depend on what else is in flight.
+ */
+PCS_API pcs_status pcs_serve_start(pcs_server **out, const pcs_server_config *cfg);
+
+/* Set up a slice size ahead of traffic (autotune, step size, tables); info may be NULL. */
+PCS_API pcs_status pcs_serve_prepare_size(pcs_server *sv, int H, int W, pcs_tuning *info);
+
+/*
+ * Open a request for a volume of S slices of H x W with regularisation lambda.
+ * chi_host: host [S][H][W] float32 that receives chi (keep it alive until the
+ * request completes).  Returns its id.  PCS_ENOMEM if the volume alone exceeds
+ * the budget, PCS_EUNSUPPORTED for a size without a kernel.
+ */
+PCS_API pcs_status pcs_serve_open(pcs_server *sv, int H, int W, int S, double lambda, float *chi_host,
+                                  long long *id);
+
+/*
+ * Slices [s0, s0+n) of request id have arrived: host field [n][H][W] float32
+ * and mask [n][H][W] uint8 (pinned memory recommended; keep them alive until
+ * the request completes).  Slices must be pushed in order.
+ */
+PCS_API pcs_status pcs_serve_push(pcs_server *sv, long long id, int s0, int n, const float *field_host,
+                                  const unsigned char *mask_host);
+
+/* Up to max finished requests since the last poll: ids and latencies (s). Non-blocking. */
+PCS_API pcs_status pcs_serve_poll(pcs_server *sv, long long *ids, double *latency_s, int max, int *n_out);
+
+/* Running statistics (latency quantiles over finished requests). */
+PCS_API pcs_status pcs_serve_stats(pcs_server *sv, pcs_serve_summary *out);
+
+/* Stop the scheduler, wait for work in flight, release everything. NULL-safe. */
+PCS_API void pcs_serve_stop(pcs_server *sv);
+
 /*
  * Solve without allocating device memory (the paper has no counterpart; this
  * is a deployment aid).  For callers that may not call cudaMalloc once they

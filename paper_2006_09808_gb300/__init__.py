@@ -96,6 +96,35 @@ class pcs_tuning(ctypes.Structure):
         }
 
 
+class pcs_server_config(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", ctypes.c_size_t),
+        ("slots", ctypes.c_int),
+        ("n_iter", ctypes.c_int),
+        ("autotune", ctypes.c_int),
+        ("b0_axis", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
+    ]
+
+
+class pcs_serve_summary(ctypes.Structure):
+    _fields_ = [
+        ("completed", ctypes.c_longlong),
+        ("pending", ctypes.c_longlong),
+        ("voxel_iters", ctypes.c_double),
+        ("span_s", ctypes.c_double),
+        ("p50_s", ctypes.c_double),
+        ("p99_s", ctypes.c_double),
+        ("max_s", ctypes.c_double),
+        ("peak_bytes", ctypes.c_double),
+        ("peak_inflight", ctypes.c_int),
+        ("pad", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 _lib = None
 
 
@@ -127,6 +156,13 @@ def load_library(path: str = LIB_PATH):
         "pcs_batch_solve": (i, [vp, ctypes.POINTER(pcs_volume), i, i]),
         "pcs_batch_tuning": (i, [vp, i, i, ctypes.POINTER(pcs_tuning)]),
         "pcs_batch_destroy": (None, [vp]),
+        "pcs_serve_start": (i, [ctypes.POINTER(vp), ctypes.POINTER(pcs_server_config)]),
+        "pcs_serve_prepare_size": (i, [vp, i, i, ctypes.POINTER(pcs_tuning)]),
+        "pcs_serve_open": (i, [vp, i, i, i, d, vp, ctypes.POINTER(ctypes.c_longlong)]),
+        "pcs_serve_push": (i, [vp, ctypes.c_longlong, i, i, vp, vp]),
+        "pcs_serve_poll": (i, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d), i, ctypes.POINTER(i)]),
+        "pcs_serve_stats": (i, [vp, ctypes.POINTER(pcs_serve_summary)]),
+        "pcs_serve_stop": (None, [vp]),
         "pcs_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -324,6 +360,62 @@ def pcs_batch_tuning(batch, H: int, W: int):
 def pcs_batch_destroy(batch):
     if batch is not None:
         load_library().pcs_batch_destroy(batch)
+
+
+def pcs_serve_start(hbm_budget_bytes: int, slots: int = 8, n_iter: int = 400, autotune: bool = True,
+                    b0_axis: int = 0):
+    """Start a serving loop (scheduler thread in libpcs); returns its handle."""
+    cfg = pcs_server_config()
+    cfg.hbm_budget_bytes, cfg.slots, cfg.n_iter = int(hbm_budget_bytes), slots, n_iter
+    cfg.autotune, cfg.b0_axis = 1 if autotune else 0, b0_axis
+    h = ctypes.c_void_p()
+    _check(load_library().pcs_serve_start(ctypes.byref(h), ctypes.byref(cfg)), "pcs_serve_start")
+    return h
+
+
+def pcs_serve_prepare_size(server, H: int, W: int):
+    t = pcs_tuning()
+    _check(load_library().pcs_serve_prepare_size(server, H, W, ctypes.byref(t)), "pcs_serve_prepare_size")
+    return t.as_dict()
+
+
+def pcs_serve_open(server, H: int, W: int, S: int, lam: float, chi_host) -> int:
+    """chi_host: numpy float32 [S][H][W] (pinned recommended), filled when the request completes."""
+    import numpy as np
+
+    c = _host_ptr(chi_host, np.float32, (S, H, W), "chi_host")
+    rid = ctypes.c_longlong()
+    _check(load_library().pcs_serve_open(server, H, W, S, lam, c, ctypes.byref(rid)), "pcs_serve_open")
+    return rid.value
+
+
+def pcs_serve_push(server, rid: int, s0: int, field_host, mask_host):
+    """Slices s0.. of request rid have arrived: numpy float32 / uint8 [n][H][W] (kept alive by the caller)."""
+    import numpy as np
+
+    n, H, W = field_host.shape
+    f = _host_ptr(field_host, np.float32, (n, H, W), "field_host")
+    m = _host_ptr(mask_host, np.uint8, (n, H, W), "mask_host")
+    _check(load_library().pcs_serve_push(server, rid, s0, n, f, m), "pcs_serve_push")
+
+
+def pcs_serve_poll(server, max_items: int = 256):
+    ids = (ctypes.c_longlong * max_items)()
+    lat = (ctypes.c_double * max_items)()
+    n = ctypes.c_int()
+    _check(load_library().pcs_serve_poll(server, ids, lat, max_items, ctypes.byref(n)), "pcs_serve_poll")
+    return [(ids[k], lat[k]) for k in range(n.value)]
+
+
+def pcs_serve_stats(server):
+    out = pcs_serve_summary()
+    _check(load_library().pcs_serve_stats(server, ctypes.byref(out)), "pcs_serve_stats")
+    return out.as_dict()
+
+
+def pcs_serve_stop(server):
+    if server is not None:
+        load_library().pcs_serve_stop(server)
 
 
 class Solver:

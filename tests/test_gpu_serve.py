@@ -1,0 +1,133 @@
+"""Serving loop: continuous batching of slice-streamed volume requests.
+
+Requests of different slice sizes are opened and their slices pushed in
+chunks while other requests run; each result must equal (bitwise) the same
+volume served alone, and the plain solve with the server's kernel variant and
+step size.  Admission respects the memory budget.
+"""
+
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2006_09808_gb300 as pcs  # noqa: E402
+import phantoms  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+N_ITER = 80
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_09808_gb300 import build
+
+    build.build()
+    pcs.load_library()
+
+
+def pinned(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+def _wait_all(sv, ids, timeout=120.0):
+    done, t0 = {}, time.time()
+    while len(done) < len(ids):
+        for rid, lat in pcs.pcs_serve_poll(sv):
+            done[rid] = lat
+        assert time.time() - t0 < timeout, "requests did not complete"
+        time.sleep(0.002)
+    return done
+
+
+def _serve(sv, probs, chunks=3, gap_s=0.003):
+    outs, keep, ids = [], [], []
+    for pb in probs:
+        S, H, W = pb.field.shape
+        f, m = pinned(pb.field), pinned(pb.mask)
+        chi = pinned(np.full(pb.field.shape, np.nan, np.float32))
+        rid = pcs.pcs_serve_open(sv, H, W, S, pb.lam, chi)
+        keep += [f, m]
+        outs.append(chi)
+        ids.append((rid, f, m, S))
+    # push the slices of all requests interleaved, in chunks, as a scanner would
+    pos = [0] * len(ids)
+    while any(p < S for p, (_, _, _, S) in zip(pos, ids)):
+        for k, (rid, f, m, S) in enumerate(ids):
+            if pos[k] < S:
+                n = max(1, -(-S // chunks))
+                n = min(n, S - pos[k])
+                pcs.pcs_serve_push(sv, rid, pos[k], f[pos[k]:pos[k] + n], m[pos[k]:pos[k] + n])
+                pos[k] += n
+                time.sleep(gap_s)
+    lat = _wait_all(sv, [r for r, *_ in ids])
+    return outs, lat
+
+
+PROBS = [
+    (128, 4, 1, 2e-4), (256, 3, 2, 5e-4), (192, 5, 3, 1e-3), (128, 3, 4, 5e-4), (384, 2, 5, 2e-4), (256, 4, 6, 1e-3),
+]
+
+
+def _probs():
+    return [phantoms.volume(H, H, S, seed=sd, lam=lam, n_iter=N_ITER) for H, S, sd, lam in PROBS]
+
+
+def test_mix_equals_alone_and_plain():
+    probs = _probs()
+    sv = pcs.pcs_serve_start(hbm_budget_bytes=8 << 30, slots=4, n_iter=N_ITER, autotune=True)
+    try:
+        tun = {H: pcs.pcs_serve_prepare_size(sv, H, H) for H, *_ in PROBS}
+        mix, lat = _serve(sv, probs)
+        st = pcs.pcs_serve_stats(sv)
+        assert st["completed"] == len(probs) and st["peak_inflight"] >= 2  # work overlapped
+        assert all(v > 0 for v in lat.values())
+        for k, pb in enumerate(probs):
+            alone, _ = _serve(sv, [pb], chunks=1)
+            assert np.array_equal(mix[k], alone[0]), k
+    finally:
+        pcs.pcs_serve_stop(sv)
+    for k, pb in enumerate(probs):
+        S, H, W = pb.field.shape
+        t = tun[H]
+        f = torch.from_numpy(pb.field).cuda()
+        m = torch.from_numpy(pb.mask).cuda()
+        chi = torch.empty_like(f)
+        ctx = pcs.pcs_create(H, W, S, cluster_size=t["cluster_size"], kernel=t["kernel"], threads=t["threads"])
+        try:
+            pcs.pcs_solve_slices(ctx, f, m, pb.lam, 1 / t["L"], 1 / t["L"], N_ITER, chi)
+            torch.cuda.synchronize()
+        finally:
+            pcs.pcs_destroy(ctx)
+        assert np.array_equal(mix[k], chi.cpu().numpy()), k
+
+
+def test_budget_limits_admission():
+    probs = _probs()[:3]
+    biggest = max(pb.voxels for pb in probs) * 25
+    sv = pcs.pcs_serve_start(hbm_budget_bytes=biggest + 1024, slots=4, n_iter=20, autotune=False)
+    try:
+        outs, _ = _serve(sv, probs)
+        st = pcs.pcs_serve_stats(sv)
+        assert st["peak_inflight"] == 1 and st["peak_bytes"] <= biggest + 1024
+        assert all(np.all(np.isfinite(o)) for o in outs)
+    finally:
+        pcs.pcs_serve_stop(sv)
+
+
+def test_rejections():
+    sv = pcs.pcs_serve_start(hbm_budget_bytes=1 << 20, slots=1, n_iter=5, autotune=False)
+    try:
+        chi = np.zeros((4, 256, 256), np.float32)
+        with pytest.raises(pcs.PcsError) as ei:  # 4 x 256 x 256 x 25 B > 1 MiB
+            pcs.pcs_serve_open(sv, 256, 256, 4, 1e-3, chi)
+        assert ei.value.status == pcs.PCS_ENOMEM
+        with pytest.raises(pcs.PcsError) as ei:
+            pcs.pcs_serve_open(sv, 100, 100, 1, 1e-3, np.zeros((1, 100, 100), np.float32))
+        assert ei.value.status == pcs.PCS_EUNSUPPORTED
+    finally:
+        pcs.pcs_serve_stop(sv)
