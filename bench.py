@@ -196,6 +196,7 @@ def run_native(args):
 
     import paper_2006_09808_gb300 as pcs
     import phantoms
+    from paper_2006_09808_gb300.sharding import max_over_ranks
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -250,10 +251,7 @@ def run_native(args):
         t_wall = time.perf_counter() - t_wall
     dev_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_step = sum(dev_ms) / len(dev_ms)
-    if dist is not None:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, device=dev)  # slowest rank sets the job time
     work = SLICES * H * W * N_ITER  # voxel-iterations per rank per step
     value = ws * work / (ms_step * 1e-3)
 
@@ -270,10 +268,7 @@ def run_native(args):
         pcs.pcs_solve_slices_host(ctx, hf, hm, LAM, tau, sigma, N_ITER, hc)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_t) / len(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, device=dev)
     dev_chi = chi.cpu().numpy()
     assert np.array_equal(dev_chi, hc), "host-buffer path differs from the device path"
 
