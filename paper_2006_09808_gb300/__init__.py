@@ -15,7 +15,8 @@ import os
 import re
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libpcs.so")
+# PCS_LIBRARY overrides the library path (e.g. a build of another configuration)
+LIB_PATH = os.environ.get("PCS_LIBRARY") or os.path.join(PKG, "libpcs.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "pcs.h")
 
 PCS_OK, PCS_EINVAL, PCS_EUNSUPPORTED, PCS_ENOMEM, PCS_ECUDA, PCS_ETIMEOUT, PCS_EBUSY = range(7)

@@ -21,10 +21,13 @@
 
 namespace pcs {
 
-template <int H_, int W_, int C_, int NT_ = 256, int ER_ = 0, int EC_ = 0>
-struct GeoRes : Geo<H_, W_, C_, 1, NT_, ER_, EC_> {
-    using B = Geo<H_, W_, C_, 1, NT_, ER_, EC_>;
-    static constexpr int WP = W_ + 16;  // plane row pitch (floats / bytes for the mask)
+// PAD_: extra floats per plane row; 16 separates the four row groups of a
+// warp onto different banks when a row group is 8 lanes wide (not needed for
+// 16-lane groups).  MINB_: CTAs per SM the register budget is set for.
+template <int H_, int W_, int C_, int NT_ = 256, int ER_ = 0, int EC_ = 0, int PAD_ = 16, int MINB_ = 1>
+struct GeoRes : Geo<H_, W_, C_, MINB_, NT_, ER_, EC_> {
+    using B = Geo<H_, W_, C_, MINB_, NT_, ER_, EC_>;
+    static constexpr int WP = W_ + PAD_;  // plane row pitch (floats / bytes for the mask)
     static constexpr int PLANE = B::R * WP;
     static constexpr size_t SMEM_BYTES = B::SMEM_BYTES + sizeof(float) * 4 * PLANE + (size_t)PLANE;
     static_assert(B::R == B::RPP, "resident kernel: one row pass per phase");
@@ -43,7 +46,7 @@ struct ResPlanes {
 };
 
 template <class G>
-__global__ void __launch_bounds__(G::NT, 1) pd_resident_kernel(PDParams prm) {
+__global__ void __launch_bounds__(G::NT, G::MINB) pd_resident_kernel(PDParams prm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Ctx<G> cx;
     ctx_init<G>(cx, smem_raw, prm.twid);
