@@ -310,6 +310,21 @@ PCS_API pcs_status pcs_solve_slices_noalloc(const float *field, const unsigned c
                                             int S, double lambda, double tau, double sigma, int n_iter,
                                             float *chi_out, int b0_axis, void *cuda_stream);
 
+/*
+ * pcs_solve_slices with monitoring: iterate in chunks of check_every
+ * iterations; after each chunk evaluate the FP64 diagnostics of every slice
+ * (as pcs_report) and, if rel_gap_tol > 0, freeze each slice whose
+ * Fenchel-Young gap is <= rel_gap_tol * objective (its chi, p, q stay as they
+ * are).  Chunks resume exactly from the stored state, so with
+ * rel_gap_tol = 0 the result equals one n_iter-iteration solve bit for bit.
+ * rep (host, S entries, required) receives each slice's last diagnostics and
+ * its iteration count.  Synchronises the stream.  (The paper's stop is the
+ * fixed count; the gap test is this library's optional monitor.)
+ */
+PCS_API pcs_status pcs_solve_slices_monitored(pcs_ctx *ctx, const float *field, const unsigned char *mask, int S,
+                                              double lambda, double tau, double sigma, int n_iter, int check_every,
+                                              double rel_gap_tol, float *chi_out, pcs_slice_report *rep);
+
 /* Release the context and everything it owns. NULL-safe. */
 PCS_API void pcs_destroy(pcs_ctx *ctx);
 

@@ -149,6 +149,7 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_slices": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_host": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_report": (i, [vp, vp, vp, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
+        "pcs_solve_slices_monitored": (i, [vp, vp, vp, i, d, d, d, i, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
         "pcs_solve_slices_noalloc": (i, [vp, vp, i, i, i, d, d, d, i, vp, i, vp]),
         "pcs_destroy": (None, [vp]),
@@ -270,6 +271,19 @@ def pcs_solve_slices_host(ctx, field, mask, lam: float, tau: float, sigma: float
     _check(load_library().pcs_solve_slices_host(ctx, f, m, S, lam, tau, sigma, n_iter, c, rep),
            "pcs_solve_slices_host")
     return [r.as_dict() for r in rep] if rep is not None else None
+
+
+def pcs_solve_slices_monitored(ctx, field, mask, lam: float, tau: float, sigma: float, n_iter: int, check_every: int,
+                               rel_gap_tol: float, chi_out):
+    """Chunked solve with FP64 diagnostics every check_every iterations and optional per-slice early stop."""
+    S, H, W = field.shape
+    f = _dev_ptr(field, "float32", (S, H, W), "field")
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
+    rep = (pcs_slice_report * max(S, 1))()
+    _check(load_library().pcs_solve_slices_monitored(ctx, f, m, S, lam, tau, sigma, n_iter, check_every,
+                                                     rel_gap_tol, c, rep), "pcs_solve_slices_monitored")
+    return [rep[k].as_dict() for k in range(S)]
 
 
 def pcs_report(ctx, field, mask, lam: float, chi):

@@ -4,6 +4,7 @@
 // twiddle tables, context-owned scratch, kernel variant selection and launch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -155,6 +156,7 @@ struct pcs_ctx {
     double* Ldev = nullptr;
     float* xa = nullptr;
     float* xb = nullptr;
+    int* active = nullptr;  // monitored solves: per-slice flags
     // CUDA-graph replay (use_graph): the last captured solve and its arguments
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -168,7 +170,7 @@ namespace {
 void free_ctx(pcs_ctx* c) {
     if (!c) return;
     void* ptrs[] = {c->dtab,     c->ddtab,  c->twid,    c->chibar, c->p,   c->qx,  c->qy,
-                    c->st_field, c->st_mask, c->st_chi, c->partials, c->Ldev, c->xa, c->xb};
+                    c->st_field, c->st_mask, c->st_chi, c->partials, c->Ldev, c->xa, c->xb, c->active};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -196,7 +198,8 @@ pcs_status validate_solve(pcs_ctx* ctx, const void* field, const void* mask, int
 
 pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
                         double tau, double sigma, int n_iter, float* chi_out,
-                        const float* inv_den_slice = nullptr) {
+                        const float* inv_den_slice = nullptr, const pcs::KernelEntry* entry = nullptr,
+                        int ncl_override = 0, int resume = 0, const int* active = nullptr) {
     if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out))
         return fail(PCS_EINVAL, "device buffers must be 16-byte aligned");
     pcs::PDParams prm;
@@ -217,11 +220,18 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     prm.tau = (float)tau;
     prm.inv_den = (float)(1.0 / (1.0 + sigma / lambda));
     prm.inv_den_slice = inv_den_slice;
-    int ncl = ctx->max_clusters;
+    prm.active = active;
+    prm.resume = resume;
+    int ncl = ncl_override > 0 ? ncl_override : ctx->max_clusters;
     if (ctx->opt.max_clusters > 0 && ctx->opt.max_clusters < ncl) ncl = ctx->opt.max_clusters;
     if (ncl > S) ncl = S;
     if (ncl < 1) ncl = 1;
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (entry && entry != ctx->entry) {  // another variant of the same size (monitored solves)
+        PCS_CUDA(entry->launch(prm, ncl, ctx->stream), "launch of the primal-dual kernel");
+        ctx->last_iters = n_iter;
+        return PCS_OK;
+    }
     if (ctx->opt.use_graph) {
         // replay the captured graph when the arguments are those it was captured with
         const bool same = ctx->graph_exec && ncl == ctx->graph_ncl &&
@@ -476,6 +486,56 @@ pcs_status pcs_opnorm(pcs_ctx* ctx, const unsigned char* mask, int S, int power_
     if (!mask || !L_out) return fail(PCS_EINVAL, "NULL argument");
     if (power_iters < 1) return fail(PCS_EINVAL, "power_iters must be >= 1");
     return pcs::ctx_opnorm(ctx, mask, S, power_iters, L_out);
+}
+
+pcs_status pcs_solve_slices_monitored(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S,
+                                      double lambda, double tau, double sigma, int n_iter, int check_every,
+                                      double rel_gap_tol, float* chi_out, pcs_slice_report* rep) {
+    pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
+    if (st != PCS_OK || S == 0) return st;
+    if (!rep) return fail(PCS_EINVAL, "rep is required");
+    if (check_every < 1) return fail(PCS_EINVAL, "check_every must be >= 1");
+    if (!(rel_gap_tol >= 0.0)) return fail(PCS_EINVAL, "rel_gap_tol must be >= 0");
+    std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
+    PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    // chunked solves resume from the stored state: a streaming variant of this size
+    const pcs::KernelEntry* e = ctx->entry->resident ? find_entry(ctx->H, ctx->W, 0, 1) : ctx->entry;
+    if (!e) return fail(PCS_EUNSUPPORTED, "no streaming kernel for %d x %d", ctx->H, ctx->W);
+    int ncl = ctx->max_clusters;
+    if (e != ctx->entry) {
+        int aux = 0;
+        PCS_CUDA(e->prepare(&ncl, &aux), "kernel attributes");
+    }
+    if (!ctx->active) PCS_CUDA(cudaMalloc(&ctx->active, (size_t)ctx->max_slices * sizeof(int)), "cudaMalloc flags");
+    std::vector<int> act(S, 1);
+    std::vector<int> iters(S, 0);
+    int done = 0;
+    while (done < n_iter) {
+        const int k = std::min(check_every, n_iter - done);
+        PCS_CUDA(cudaMemcpyAsync(ctx->active, act.data(), S * sizeof(int), cudaMemcpyHostToDevice, ctx->stream),
+                 "flags upload");
+        st = launch_solve(ctx, field, mask, S, lambda, tau, sigma, k, chi_out, nullptr, e, ncl, done > 0 ? 1 : 0,
+                          ctx->active);
+        if (st != PCS_OK) return st;
+        done += k;
+        for (int s = 0; s < S; ++s)
+            if (act[s]) iters[s] = done;
+        // FP64 diagnostics of every slice (frozen slices keep their last state)
+        std::vector<pcs_slice_report> r(S);
+        st = pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, r.data());
+        if (st != PCS_OK) return st;
+        int n_active = 0;
+        for (int s = 0; s < S; ++s) {
+            if (act[s]) rep[s] = r[s];
+            rep[s].iters = iters[s];
+            if (act[s] && rel_gap_tol > 0.0 && r[s].gap <= rel_gap_tol * std::max(r[s].objective, 1e-300)) act[s] = 0;
+            n_active += act[s];
+        }
+        if (n_active == 0) break;
+    }
+    ctx->last_iters = done;
+    return PCS_OK;
 }
 
 void pcs_destroy(pcs_ctx* ctx) { free_ctx(ctx); }

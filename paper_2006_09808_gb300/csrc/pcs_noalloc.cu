@@ -25,6 +25,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -161,6 +162,7 @@ extern "C" pcs_status pcs_solve_slices_noalloc(const float* field, const unsigne
 
     const size_t n = (size_t)S * H * W;
     pcs::PDParams prm;
+    std::memset(&prm, 0, sizeof(prm));
     prm.field = field;
     prm.mask = mask;
     prm.chi = chi_out;

@@ -63,6 +63,8 @@ struct PDParamsT {
     Real tau;
     Real inv_den;               // 1 / (1 + sigma / lambda)
     const Real* inv_den_slice;  // NULL, or per-slice 1 / (1 + sigma / lambda_s) [S]
+    const int* active;          // NULL, or per-slice flag [S]: 0 = leave this slice untouched
+    int resume;                 // 0: zero start; 1: continue from chi (chi_out), chibar, p, q
 };
 using PDParams = PDParamsT<float>;
 
@@ -470,11 +472,33 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
                 cn.y = chi[c].y - tau * v.y - tau * d1;
                 __stcg(reinterpret_cast<V*>(chip + o), cn);
                 const V cb = mk<V>(Real(2) * cn.x - chi[c].x, Real(2) * cn.y - chi[c].y);
-                if (!last) __stcg(reinterpret_cast<V*>(cbar + o), cb);
+                __stcg(reinterpret_cast<V*>(cbar + o), cb);  // kept for a later resume
                 x[e] = cb;
             }
         }
         if (!last) row_forward<G>(cx, rs, i, g, gm, x);
+    }
+}
+
+// Forward real row transforms of a stored field (own rows) and scatter: the
+// spectrum a resumed solve starts from.
+template <class G>
+__device__ __forceinline__ void rows_forward_state(const Ctx<G>& cx, const typename G::Real* src, size_t base) {
+    using V = typename G::V;
+    constexpr int W = G::W, TR = G::TR, ER = G::ER;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % TR;
+    const int grp = warp * (32 / TR) + lane / TR;
+    const unsigned gm = group_mask<TR>(lane);
+    V* rs = cx.rows + grp * G::MP;
+#pragma unroll 1
+    for (int pass = 0; pass < G::R / G::RPP; ++pass) {
+        const int i = cx.crank * G::R + pass * G::RPP + grp;
+        const size_t rowoff = base + (size_t)i * W;
+        V z[ER];
+#pragma unroll
+        for (int e = 0; e < ER; ++e) z[e] = __ldcg(reinterpret_cast<const V*>(src + rowoff + 2 * (g + TR * e)));
+        row_forward<G>(cx, rs, i, g, gm, z);
     }
 }
 
@@ -495,8 +519,27 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParamsT<ty
 
 #pragma unroll 1
     for (int s = cid; s < prm.S; s += ncl) {
+        if (prm.active && __ldg(prm.active + s) == 0) continue;  // same decision in every CTA of the cluster
         const size_t base = (size_t)s * SLICE;
         const Real inv_den = slice_inv_den(prm, s);
+        if (prm.resume) {
+            // continue: the spectrum of the stored chibar, then the loop as after iteration 0
+            cluster_barrier<G::C>();  // peers running before their shared memory is written
+            rows_forward_state<G>(cx, prm.chibar, base);
+            cluster_barrier<G::C>();
+#pragma unroll 1
+            for (int n = 0; n < prm.n_iter; ++n) {
+                column_pass<G>(cx, prm.dtab, prm.ddtab);
+                cluster_barrier<G::C>();
+                phase_dual<G>(cx, prm, base, inv_den);
+                cluster_barrier<G::C>();
+                column_pass<G>(cx, prm.dtab, prm.ddtab);
+                cluster_barrier<G::C>();
+                phase_primal<G>(cx, prm, base, n + 1 == prm.n_iter);
+                cluster_barrier<G::C>();
+            }
+            continue;
+        }
         // zero start (pseudocode steps 2-3): chi, chibar, p, q of own rows, own spectrum
         {
             const size_t o = base + (size_t)cx.crank * OWN;
