@@ -72,7 +72,10 @@ typedef struct pcs_options {
     int threads;       /* 0 = library default; else threads per CTA of a compiled variant */
     int use_graph;     /* 1 = launch each solve as a CUDA graph, captured once per distinct argument
                           set and replayed (needs a non-NULL stream); 0 = direct launch */
-    int reserved[2];
+    int tv;            /* 0 = anisotropic TV: the dual TV prox clamps each gradient component
+                          (the componentwise reading of Eq. (1)'s ||M G chi||_1, default);
+                          1 = isotropic TV: it projects each pixel's (qx, qy) onto the unit disc */
+    int reserved[1];
 } pcs_options;
 
 /* Diagnostics of one slice at (chi_N, p_N, q_N), in FP64 (see pcs_slice_report doc below). */

@@ -27,6 +27,8 @@ Readings of the paper taken here (the paper is silent or ambiguous on each):
   b = W * dB, which is the exact prox of the Eq. (1) data term.
 * The norm in the TV dual prox is taken componentwise (anisotropic), the
   literal dual of the l1 norm in Eq. (1): the prox is a clamp to [-1, 1].
+  ``tv="iso"`` takes the other reading (pointwise Euclidean norm, isotropic
+  TV): the prox projects (qx, qy) onto the unit disc.
 * The primal function is zero, so prox_tau[G] is the identity: the primal
   step is chi - tau K^T y.
 * Fixed iteration count N; the output is chi_N (not chi-bar).
@@ -137,6 +139,14 @@ def prox_dual_tv(v: np.ndarray) -> np.ndarray:
     return clamp_unit(v)
 
 
+def prox_dual_tv_iso(vx: np.ndarray, vy: np.ndarray):
+    """Isotropic reading: F2 = sum of pointwise Euclidean norms of (gx, gy); its
+    conjugate's prox projects each (vx, vy) onto the unit disc:
+    v / max(1, |v|_2)."""
+    n = np.maximum(1.0, np.sqrt(vx * vx + vy * vy))
+    return vx / n, vy / n
+
+
 # --------------------------------------------------------------------------- solver
 
 
@@ -162,13 +172,16 @@ def pd_solve(
     tv_mask: np.ndarray | None = None,
     theta: float = 1.0,
     return_state: bool = False,
+    tv: str = "aniso",
 ):
     """Run N iterations of the Sec. II.A primal-dual pseudocode in FP64.
 
     ``field`` (dB, ppm) and ``mask`` are [H][W] or [S][H][W]; slices are
     solved independently.  W = ``weight`` (default: mask) and M = ``tv_mask``
-    (default: mask).  Returns chi_N (float64), or the full state when
-    ``return_state`` is true.
+    (default: mask).  ``tv``: "aniso" reads the norm of the TV dual prox
+    componentwise (clamp), "iso" pointwise Euclidean (projection onto the unit
+    disc).  Returns chi_N (float64), or the full state when ``return_state``
+    is true.
     """
     f = np.asarray(field, dtype=np.float64)
     m = np.asarray(mask, dtype=np.float64)
@@ -188,10 +201,13 @@ def pd_solve(
     for _ in range(n_iter):
         # dual data prox: p <- (p + sigma (W D chi_bar - dB_w)) / (1 + sigma/lambda)
         p = prox_dual_data(p + sigma * (Wt * apply_D(chi_bar, Dk)), b, sigma, lam)
-        # dual TV prox: q <- clamp(q + sigma M G chi_bar)
+        # dual TV prox: q <- (q + sigma M G chi_bar) / max(1, |.|)
         gx, gy = grad(chi_bar)
-        qx = prox_dual_tv(qx + sigma * Mt * gx)
-        qy = prox_dual_tv(qy + sigma * Mt * gy)
+        if tv == "iso":
+            qx, qy = prox_dual_tv_iso(qx + sigma * Mt * gx, qy + sigma * Mt * gy)
+        else:
+            qx = prox_dual_tv(qx + sigma * Mt * gx)
+            qy = prox_dual_tv(qy + sigma * Mt * gy)
         # primal step: chi+ = chi - tau D^T W^T p - tau G^T M^T q  (prox of 0 = identity)
         chi_new = chi - tau * apply_D(Wt * p, Dk) - tau * grad_adjoint(Mt * qx, Mt * qy)
         # over-relaxation: chi_bar = chi+ + theta (chi+ - chi)
@@ -222,6 +238,7 @@ def diagnostics(
     b0_axis: int = 0,
     weight: np.ndarray | None = None,
     tv_mask: np.ndarray | None = None,
+    tv: str = "aniso",
 ) -> Diagnostics:
     """Objective, Fenchel-Young gap and stationarity of Eq. (1) at (chi, p, q).
 
@@ -242,9 +259,13 @@ def diagnostics(
     gx, gy = grad(state.chi)
     gx, gy = Mt * gx, Mt * gy
     r = z - b
-    primal = 0.5 * lam * float(np.sum(r * r)) + float(np.sum(np.abs(gx)) + np.sum(np.abs(gy)))
+    if tv == "iso":
+        tvn = float(np.sum(np.sqrt(gx * gx + gy * gy)))
+    else:
+        tvn = float(np.sum(np.abs(gx)) + np.sum(np.abs(gy)))
+    primal = 0.5 * lam * float(np.sum(r * r)) + tvn
     fy1 = float(np.sum((state.p - lam * r) ** 2)) / (2.0 * lam)
-    fy2 = float(np.sum(np.abs(gx) - state.qx * gx) + np.sum(np.abs(gy) - state.qy * gy))
+    fy2 = tvn - float(np.sum(state.qx * gx) + np.sum(state.qy * gy))
     kty = apply_D(Wt * state.p, Dk) + grad_adjoint(Mt * state.qx, Mt * state.qy)
     return Diagnostics(
         primal=primal,

@@ -38,7 +38,8 @@ class pcs_options(ctypes.Structure):
         ("kernel", ctypes.c_int),
         ("threads", ctypes.c_int),
         ("use_graph", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("tv", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 
@@ -228,7 +229,8 @@ KERNEL_DEFAULT, KERNEL_STREAMING, KERNEL_RESIDENT = 0, 1, 2
 
 
 def pcs_create(H: int, W: int, max_slices: int, b0_axis: int = 0, cluster_size: int = 0, max_clusters: int = 0,
-               kernel: int = KERNEL_DEFAULT, threads: int = 0, use_graph: bool = False, stream=None):
+               kernel: int = KERNEL_DEFAULT, threads: int = 0, use_graph: bool = False, tv: int = 0,
+               stream=None):
     """Create a context; returns an opaque handle (c_void_p).  stream: torch.cuda.Stream or None (current)."""
     import torch
 
@@ -238,6 +240,7 @@ def pcs_create(H: int, W: int, max_slices: int, b0_axis: int = 0, cluster_size: 
     opt.b0_axis, opt.cluster_size, opt.max_clusters, opt.kernel = b0_axis, cluster_size, max_clusters, kernel
     opt.threads = threads
     opt.use_graph = 1 if use_graph else 0
+    opt.tv = tv
     s = (stream or torch.cuda.current_stream()).cuda_stream
     h = ctypes.c_void_p()
     _check(lib.pcs_create(ctypes.byref(h), H, W, max_slices, ctypes.byref(opt), ctypes.c_void_p(s)), "pcs_create")

@@ -222,6 +222,7 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     prm.inv_den_slice = inv_den_slice;
     prm.active = active;
     prm.resume = resume;
+    prm.tv_iso = ctx->opt.tv;
     int ncl = ncl_override > 0 ? ncl_override : ctx->max_clusters;
     if (ctx->opt.max_clusters > 0 && ctx->opt.max_clusters < ncl) ncl = ctx->opt.max_clusters;
     if (ncl > S) ncl = S;
@@ -317,6 +318,7 @@ pcs_status ctx_report(pcs_ctx* c, const float* field, const unsigned char* mask,
     a.mask = mask;
     a.chi = chi;
     a.lam = (float)lambda;
+    a.tv_iso = c->opt.tv;
     PCS_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
     PCS_CUDA(c->entry->launch_report(a, aux_clusters(c, S), c->stream), "launch of the report kernel");
     const int C = c->entry->C;
@@ -373,6 +375,7 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
     if (opt) o = *opt;
     if (o.b0_axis != 0 && o.b0_axis != 1) return fail(PCS_EINVAL, "b0_axis must be 0 or 1");
     if (o.kernel < 0 || o.kernel > 2) return fail(PCS_EINVAL, "kernel must be 0, 1 or 2");
+    if (o.tv != 0 && o.tv != 1) return fail(PCS_EINVAL, "tv must be 0 (anisotropic) or 1 (isotropic)");
     if (o.use_graph && cuda_stream == nullptr)
         return fail(PCS_EINVAL, "use_graph needs a non-NULL stream (the legacy stream cannot be captured)");
     const pcs::KernelEntry* entry = find_entry(H, W, o.cluster_size, o.kernel, o.threads);

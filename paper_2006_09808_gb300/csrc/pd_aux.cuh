@@ -34,6 +34,7 @@ struct AuxParams {
     int S;
     float lam;
     int iters;
+    int tv_iso;
 };
 
 constexpr int kReportSums = 5;  // data_sq, tv_l1, fy1_sq, fy2, stat_sq
@@ -139,11 +140,12 @@ __global__ void __launch_bounds__(G::NT, 1) aux_report_kernel(AuxParams prm) {
                 for (int t = 0; t < 2; ++t) {
                     const double r = (double)m[t] * ((double)u[t] - (double)ff[t]);
                     acc[0] += r * r;
-                    acc[1] += fabs((double)gx[t]) + fabs((double)gy[t]);
+                    const double gxd = gx[t], gyd = gy[t];
+                    const double tvn = prm.tv_iso ? sqrt(gxd * gxd + gyd * gyd) : fabs(gxd) + fabs(gyd);
+                    acc[1] += tvn;
                     const double d1 = (double)pp[t] - (double)lam * r;
                     acc[2] += d1 * d1;
-                    acc[3] += (fabs((double)gx[t]) - (double)qxs[t] * gx[t]) +
-                              (fabs((double)gy[t]) - (double)qys[t] * gy[t]);
+                    acc[3] += tvn - ((double)qxs[t] * gxd + (double)qys[t] * gyd);
                 }
                 x[e] = make_float2(m[0] * p.x, m[1] * p.y);
             }

@@ -65,7 +65,22 @@ struct PDParamsT {
     const Real* inv_den_slice;  // NULL, or per-slice 1 / (1 + sigma / lambda_s) [S]
     const int* active;          // NULL, or per-slice flag [S]: 0 = leave this slice untouched
     int resume;                 // 0: zero start; 1: continue from chi (chi_out), chibar, p, q
+    int tv_iso;                 // 0: componentwise clamp (anisotropic TV); 1: unit-disc projection (isotropic)
 };
+
+// Dual TV prox of one pixel: v = q + sigma M G chibar; clamp each component, or
+// project (vx, vy) onto the unit disc.
+template <class Real>
+__device__ __forceinline__ void tv_prox(Real& vx, Real& vy, int iso) {
+    if (iso) {
+        const Real n = fmax(Real(1), sqrt(vx * vx + vy * vy));
+        vx = vx / n;
+        vy = vy / n;
+    } else {
+        vx = fmin(Real(1), fmax(Real(-1), vx));
+        vy = fmin(Real(1), fmax(Real(-1), vy));
+    }
+}
 using PDParams = PDParamsT<float>;
 
 template <class Real>
@@ -149,7 +164,6 @@ struct Ctx {
     V* tw;       // twiddles [NTW]
     V* stw_r;    // stage twiddles of the row transforms
     V* stw_c;    // stage twiddles of the column transforms
-    V* tb[G::C]; // spectrum columns of every CTA of the cluster (DSMEM)
     int crank;
 };
 
@@ -168,16 +182,12 @@ __device__ __forceinline__ void ctx_init(Ctx<G>& cx, unsigned char* smem_raw, co
     StageTw<G::H, G::EC>::fill(cx.stw_c, twid, G::NTW / G::H, threadIdx.x, G::NT);
     if constexpr (G::C == 1) {
         cx.crank = 0;
-        cx.tb[0] = cx.tbuf;
     } else {
-        cg::cluster_group cluster = cg::this_cluster();
-        cx.crank = (int)cluster.block_rank();
-#pragma unroll
-        for (int q = 0; q < G::C; ++q) cx.tb[q] = cluster.map_shared_rank(cx.tbuf, q);
+        cx.crank = (int)cg::this_cluster().block_rank();
     }
 }
 
-// Spectrum columns of cluster CTA q (run-time rank).
+// Spectrum columns of cluster CTA q (mapped at each use: holding C pointers costs registers).
 template <class G>
 __device__ __forceinline__ typename G::V* remote_tbuf(const Ctx<G>& cx, int q) {
     if constexpr (G::C == 1) {
@@ -252,7 +262,7 @@ __device__ __forceinline__ void row_inverse(const Ctx<G>& cx, typename G::V* rs,
             if constexpr (G::STATIC_OWNER) {
                 const int q = (TR * e) / MC;  // compile-time after unrolling
                 const int cl = k - q * MC;
-                t[e] = cx.tb[q][cl * G::HP + P(i)];
+                t[e] = remote_tbuf<G>(cx, q)[cl * G::HP + P(i)];
             } else {
                 const int q = k / MC;
                 const int cl = k - q * MC;
@@ -313,7 +323,7 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
         if constexpr (G::STATIC_OWNER) {
             const int q = (TR * e) / MC;
             const int cl = k - q * MC;
-            cx.tb[q][cl * G::HP + P(i)] = out;
+            remote_tbuf<G>(cx, q)[cl * G::HP + P(i)] = out;
         } else {
             const int q = k / MC;
             const int cl = k - q * MC;
@@ -396,10 +406,12 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
                 pn.y = (p[c].y + sigma * (m1 * (u.y - f[c].y))) * inv_den;
                 // dual TV prox (forward differences of chibar, Neumann boundary)
                 V qxn, qyn;
-                qxn.x = fmin(Real(1), fmax(-Real(1), qx[c].x + sigma * m0 * (cb[e].y - cb[e].x)));
-                qxn.y = fmin(Real(1), fmax(-Real(1), qx[c].y + sigma * m1 * (right - cb[e].y)));
-                qyn.x = fmin(Real(1), fmax(-Real(1), qy[c].x + sigma * m0 * (cd[c].x - cb[e].x)));
-                qyn.y = fmin(Real(1), fmax(-Real(1), qy[c].y + sigma * m1 * (cd[c].y - cb[e].y)));
+                qxn.x = qx[c].x + sigma * m0 * (cb[e].y - cb[e].x);
+                qxn.y = qx[c].y + sigma * m1 * (right - cb[e].y);
+                qyn.x = qy[c].x + sigma * m0 * (cd[c].x - cb[e].x);
+                qyn.y = qy[c].y + sigma * m1 * (cd[c].y - cb[e].y);
+                tv_prox(qxn.x, qyn.x, prm.tv_iso);
+                tv_prox(qxn.y, qyn.y, prm.tv_iso);
                 __stcg(reinterpret_cast<V*>(pp + o), pn);
                 __stcg(reinterpret_cast<V*>(qxp + o), qxn);
                 __stcg(reinterpret_cast<V*>(qyp + o), qyn);

@@ -138,10 +138,12 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd_resident_kernel(PDParams pr
                     pv[e].y = (pv[e].y + sigma * (m1 * (u.y - f.y))) * inv_den;
                     float2 qx = *reinterpret_cast<const float2*>(pl.qx + o);
                     float2 qy = *reinterpret_cast<const float2*>(pl.qy + o);
-                    qx.x = fminf(1.f, fmaxf(-1.f, qx.x + sigma * m0 * (cb.y - cb.x)));
-                    qx.y = fminf(1.f, fmaxf(-1.f, qx.y + sigma * m1 * (right - cb.y)));
-                    qy.x = fminf(1.f, fmaxf(-1.f, qy.x + sigma * m0 * (cd.x - cb.x)));
-                    qy.y = fminf(1.f, fmaxf(-1.f, qy.y + sigma * m1 * (cd.y - cb.y)));
+                    qx.x = qx.x + sigma * m0 * (cb.y - cb.x);
+                    qx.y = qx.y + sigma * m1 * (right - cb.y);
+                    qy.x = qy.x + sigma * m0 * (cd.x - cb.x);
+                    qy.y = qy.y + sigma * m1 * (cd.y - cb.y);
+                    tv_prox(qx.x, qy.x, prm.tv_iso);
+                    tv_prox(qx.y, qy.y, prm.tv_iso);
                     *reinterpret_cast<float2*>(pl.qx + o) = qx;
                     *reinterpret_cast<float2*>(pl.qy + o) = qy;
                     x[e] = pv[e];  // W p = p (p vanishes outside the mask)

@@ -60,6 +60,10 @@ def test_host_side_argument_checks(lib):
     bad = pcs.pcs_options()
     bad.b0_axis = 3
     assert lib.pcs_create(ctypes.byref(h), 64, 64, 4, ctypes.byref(bad), None) == pcs.PCS_EINVAL
+    bad = pcs.pcs_options()
+    bad.tv = 2
+    assert lib.pcs_create(ctypes.byref(h), 64, 64, 4, ctypes.byref(bad), None) == pcs.PCS_EINVAL
+    assert "tv" in pcs.last_error()
     assert lib.pcs_solve_slices(None, None, None, 1, 1.0, 1.0, 1.0, 1, None, None) == pcs.PCS_EINVAL
     assert lib.pcs_opnorm(None, None, 1, 10, None) == pcs.PCS_EINVAL
     lib.pcs_destroy(None)  # NULL-safe

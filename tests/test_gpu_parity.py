@@ -318,6 +318,50 @@ def test_report_matches_oracle_diagnostics():
         assert r["gap"] >= 0
 
 
+# --------------------------------------------------------------------------- isotropic TV
+
+
+@pytest.mark.parametrize(
+    "H,S,n_iter,kernel,cluster_size",
+    [(64, 3, 300, RESIDENT, 0), (64, 3, 300, STREAMING, 1), (128, 2, 150, RESIDENT, 4),
+     (256, 2, 100, STREAMING, 4), (256, 2, 100, RESIDENT, 8)],
+)
+def test_isotropic_tv_parity(H, S, n_iter, kernel, cluster_size):
+    """tv = 1: the dual TV prox projects each pixel's (qx, qy) onto the unit
+    disc; against the oracle's isotropic reading of Eq. (1)."""
+    pb = phantoms.volume(H, H, S, seed=31, lam=1.0, n_iter=n_iter)  # lambda large enough for |q| to reach 1
+    L, tau, sigma = steps(H, H)
+    ref = O.pd_solve(pb.field.astype(np.float64), pb.mask, pb.lam, tau, sigma, n_iter, tv="iso")
+    got = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, n_iter, kernel=kernel, cluster_size=cluster_size, tv=1)
+    aniso = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, n_iter, kernel=kernel, cluster_size=cluster_size)
+    for s in range(S):
+        assert rel_l2(got[s], ref[s]) <= TOL, s
+        # the two readings give different minimisers on these phantoms
+        assert rel_l2(got[s], aniso[s]) > 100 * TOL, s
+
+
+def test_isotropic_tv_report_matches_oracle_diagnostics():
+    pb = phantoms.volume(64, 64, 2, seed=4, lam=10.0, n_iter=200)
+    L, tau, sigma = steps(64, 64)
+    f = torch.from_numpy(pb.field).cuda()
+    m = torch.from_numpy(pb.mask).cuda()
+    chi = torch.empty_like(f)
+    ctx = pcs.pcs_create(64, 64, 2, tv=1)
+    try:
+        rep = pcs.pcs_solve_slices(ctx, f, m, pb.lam, tau, sigma, pb.n_iter, chi, report=True)
+    finally:
+        pcs.pcs_destroy(ctx)
+    for s in range(2):
+        st = O.pd_solve(pb.field[s].astype(np.float64), pb.mask[s], pb.lam, tau, sigma, pb.n_iter,
+                        return_state=True, tv="iso")
+        d = O.diagnostics(st, pb.field[s].astype(np.float64), pb.mask[s], pb.lam, tv="iso")
+        r = rep[s]
+        assert r["objective"] == pytest.approx(d.primal, rel=1e-4)
+        assert r["gap"] == pytest.approx(d.gap, rel=2e-2, abs=1e-4 * d.primal)
+        assert r["stationarity"] == pytest.approx(d.stationarity, rel=2e-2, abs=1e-4)
+        assert r["gap"] >= 0
+
+
 @pytest.mark.parametrize("H,kind", [(64, "full"), (256, "full"), (128, "ellipse")])
 def test_opnorm_matches_oracle(H, kind):
     mask = np.ones((H, H), np.uint8) if kind == "full" else phantoms.ellipse_mask(H, H)

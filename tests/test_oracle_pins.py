@@ -405,3 +405,46 @@ def test_gap_decreases_on_phantom():
         st = O.pd_solve(f, m, 10.0, 1 / L, 1 / L, n, return_state=True)
         gaps.append(O.diagnostics(st, f, m, 10.0).gap)
     assert gaps[0] > gaps[1] > gaps[2] >= 0
+
+
+# --------------------------------------------------------------------------- isotropic TV reading
+
+
+def test_iso_prox_is_disc_projection():
+    rng = np.random.default_rng(31)
+    vx, vy = rng.standard_normal((2, 200)) * 1.5
+    px, py = O.prox_dual_tv_iso(vx, vy)
+    assert np.all(px * px + py * py <= 1 + 1e-12)
+    inside = vx * vx + vy * vy <= 1
+    assert np.array_equal(px[inside], vx[inside]) and np.array_equal(py[inside], vy[inside])
+    # outside: the nearest point of the disc is on the same ray (brute force on a fine circle)
+    th = np.linspace(0, 2 * np.pi, 200001)
+    for k in np.nonzero(~inside)[0][:10]:
+        d = (np.cos(th) - vx[k]) ** 2 + (np.sin(th) - vy[k]) ** 2
+        t = th[np.argmin(d)]
+        assert abs(px[k] - np.cos(t)) < 1e-4 and abs(py[k] - np.sin(t)) < 1e-4
+
+
+def test_iso_equals_aniso_on_single_row_slices():
+    # with one row G_y = 0, so the pointwise Euclidean norm is the absolute value
+    rng = np.random.default_rng(32)
+    f = rng.standard_normal((3, 1, 24))
+    m = np.ones((3, 1, 24))
+    a = O.pd_solve(f, m, 2.0, 0.3, 0.3, 80, tv="aniso")
+    b = O.pd_solve(f, m, 2.0, 0.3, 0.3, 80, tv="iso")
+    assert np.allclose(a, b, rtol=0, atol=1e-15)
+
+
+def test_iso_gap_and_stationarity_vanish_8x8():
+    rng = np.random.default_rng(33)
+    f = rng.standard_normal((8, 8))
+    m = np.ones((8, 8))
+    m[2, 5] = 0
+    L = O.opnorm(np.ones((8, 8)))
+    st = O.pd_solve(f, m, 30.0, 1 / L, 1 / L, 10000, return_state=True, tv="iso")
+    dg = O.diagnostics(st, f, m, 30.0, tv="iso")
+    assert 0 <= dg.gap < 1e-9 and dg.stationarity < 1e-8
+    assert np.all(st.qx ** 2 + st.qy ** 2 <= 1 + 1e-12)
+    # the iso solution differs from the aniso one (the readings are not equivalent)
+    st2 = O.pd_solve(f, m, 30.0, 1 / L, 1 / L, 10000, return_state=True)
+    assert np.linalg.norm(st.chi - st2.chi) > 1e-6 * np.linalg.norm(st2.chi)
