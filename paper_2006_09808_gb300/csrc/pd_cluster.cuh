@@ -22,7 +22,11 @@
 //
 // The real row transforms use the half-length complex FFT of
 // z[n] = x[2n] + i x[2n+1]; the packed row spectrum stores X[0] + i X[W/2] in
-// column 0.  The column pass handles that packed column by pairing ky with -ky
+// column 0.  Splitting that FFT into the real row's spectrum (and merging it
+// back) pairs column k with column M-k of the same row; in the lane layout of
+// the transforms (lane g holds k = g + TR*e) the partner sits in lane TR-g at
+// element ER-1-e (lane 0: its own element ER-e), so the pairing is a warp
+// shuffle.  The column pass handles that packed column by pairing ky with -ky
 // (both halves are spectra of real columns):
 //   Y[ky] = Dm[ky] C[ky] + Dd[ky] conj(C[-ky]),  Dm,Dd = (D(ky,0) +- D(ky,W/2))/2.
 // All normalisation (1/(H W)) is folded into the D table.
@@ -245,6 +249,36 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const typename G::
 }
 
 // ------------------------------------------------------------------ row transforms
+// Pair every element of a row with its mirror column M-k (see the file
+// comment) and apply op(k, X[k], X[M-k]) in place.  Elements are taken in pairs
+// (e, ER-1-e), whose mirrors in lanes g >= 1 are each other's; lane 0's
+// mirrors are its own elements ER-e, read before they are overwritten (one
+// carried value).
+template <class G, class Op>
+__device__ __forceinline__ void mirror_pairs(typename G::V (&x)[G::ER], int g, unsigned gm, Op op) {
+    using V = typename G::V;
+    constexpr int TR = G::TR, ER = G::ER;
+    static_assert(ER % 2 == 0, "element pairs");
+    const int lane = threadIdx.x & 31;
+    const int src = (lane - g) + ((TR - g) & (TR - 1));  // mirror lane in the group
+    V carry = x[0];
+#pragma unroll
+    for (int e = 0; e < ER / 2; ++e) {
+        const int e2 = ER - 1 - e;
+        const V a = x[e], b = x[e2];
+        V va, vb;
+        va.x = __shfl_sync(gm, b.x, src);
+        va.y = __shfl_sync(gm, b.y, src);
+        vb.x = __shfl_sync(gm, a.x, src);
+        vb.y = __shfl_sync(gm, a.y, src);
+        const V own_a = (e == 0) ? a : carry;           // lane 0: element ER-e
+        const V own_b = (e + 1 == e2) ? b : x[e + 1];   // lane 0: element e+1
+        carry = b;
+        x[e] = op(g + TR * e, a, (g == 0) ? own_a : va);
+        x[e2] = op(g + TR * e2, b, (g == 0) ? own_b : vb);
+    }
+}
+
 // Gather packed spectrum row i from the cluster and apply the inverse real
 // row transform.  Result: x[e] = W * (y[2n], y[2n+1]) for n = g + TR*e, where
 // y is the real row (the D table carries 1/(HW), so x is the true D-product).
@@ -252,43 +286,27 @@ template <class G>
 __device__ __forceinline__ void row_inverse(const Ctx<G>& cx, typename G::V* rs, int i, int g, unsigned gm,
                                             typename G::V (&x)[G::ER]) {
     using V = typename G::V;
-    using Real = typename G::Real;
     constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
-    {
-        V t[ER];  // all remote loads in flight before any local store
-#pragma unroll
-        for (int e = 0; e < ER; ++e) {
-            const int k = g + TR * e;
-            if constexpr (G::STATIC_OWNER) {
-                const int q = (TR * e) / MC;  // compile-time after unrolling
-                const int cl = k - q * MC;
-                t[e] = remote_tbuf<G>(cx, q)[cl * G::HP + P(i)];
-            } else {
-                const int q = k / MC;
-                const int cl = k - q * MC;
-                t[e] = remote_tbuf<G>(cx, q)[cl * G::HP + P(i)];
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < ER; ++e) rs[P(g + TR * e)] = t[e];
-    }
-    __syncwarp(gm);
 #pragma unroll
     for (int e = 0; e < ER; ++e) {
         const int k = g + TR * e;
-        const V X = rs[P(k)];
-        if (k == 0) {
-            // X[0] = Re, X[M] = Im of the packed entry
-            x[e] = mk<V>(X.x + X.y, X.x - X.y);
+        if constexpr (G::STATIC_OWNER) {
+            const int q = (TR * e) / MC;  // compile-time after unrolling
+            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + P(i)];
         } else {
-            const V Xm = rs[P(M - k)];
-            const V ec = mk<V>(X.x + Xm.x, X.y - Xm.y);   // X + conj(Xm)
-            const V od0 = mk<V>(X.x - Xm.x, X.y + Xm.y);  // X - conj(Xm)
-            const V w = cx.tw[k * (NTW / W)];                    // exp(-2 pi i k / W)
-            const V od = cmul(od0, conjf2(w));
-            x[e] = mk<V>(ec.x - od.y, ec.y + od.x);  // ec + i od
+            const int q = k / MC;
+            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + P(i)];
         }
     }
+    const V* tw = cx.tw;
+    mirror_pairs<G>(x, g, gm, [tw](int k, V X, V Xm) {
+        if (k == 0) return mk<V>(X.x + X.y, X.x - X.y);  // X[0] = Re, X[M] = Im of the packed entry
+        const V ec = mk<V>(X.x + Xm.x, X.y - Xm.y);     // X + conj(Xm)
+        const V od0 = mk<V>(X.x - Xm.x, X.y + Xm.y);    // X - conj(Xm)
+        const V w = tw[k * (NTW / W)];                    // exp(-2 pi i k / W)
+        const V od = cmul(od0, conjf2(w));
+        return mk<V>(ec.x - od.y, ec.y + od.x);  // ec + i od
+    });
     fft<M, TR, true>(x, rs, cx.stw_r, g, gm);
 }
 
@@ -301,36 +319,27 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
     using Real = typename G::Real;
     constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
     fft<M, TR, false>(z, rs, cx.stw_r, g, gm);
-#pragma unroll
-    for (int e = 0; e < ER; ++e) rs[P(g + TR * e)] = z[e];
-    __syncwarp(gm);
+    const V* tw = cx.tw;
+    mirror_pairs<G>(z, g, gm, [tw](int k, V A, V Zm) {
+        if (k == 0) return mk<V>(A.x + A.y, A.x - A.y);  // X[0] + i X[M]
+        // E = (A + conj(Zm))/2, O = -i (A - conj(Zm))/2, X = E + w^k O
+        const V E = mk<V>(Real(0.5) * (A.x + Zm.x), Real(0.5) * (A.y - Zm.y));
+        const V dlt = mk<V>(A.x - Zm.x, A.y + Zm.y);
+        const V O = mk<V>(Real(0.5) * dlt.y, -Real(0.5) * dlt.x);
+        const V w = tw[k * (NTW / W)];
+        return cadd(E, cmul(w, O));
+    });
 #pragma unroll
     for (int e = 0; e < ER; ++e) {
         const int k = g + TR * e;
-        const V A = z[e];
-        V out;
-        if (k == 0) {
-            out = mk<V>(A.x + A.y, A.x - A.y);  // X[0] + i X[M]
-        } else {
-            const V Zm = rs[P(M - k)];
-            // E = (A + conj(Zm))/2, O = -i (A - conj(Zm))/2, X = E + w^k O
-            const V E = mk<V>(Real(0.5) * (A.x + Zm.x), Real(0.5) * (A.y - Zm.y));
-            const V dlt = mk<V>(A.x - Zm.x, A.y + Zm.y);
-            const V O = mk<V>(Real(0.5) * dlt.y, -Real(0.5) * dlt.x);
-            const V w = cx.tw[k * (NTW / W)];
-            out = cadd(E, cmul(w, O));
-        }
         if constexpr (G::STATIC_OWNER) {
             const int q = (TR * e) / MC;
-            const int cl = k - q * MC;
-            remote_tbuf<G>(cx, q)[cl * G::HP + P(i)] = out;
+            remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + P(i)] = z[e];
         } else {
             const int q = k / MC;
-            const int cl = k - q * MC;
-            remote_tbuf<G>(cx, q)[cl * G::HP + P(i)] = out;
+            remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + P(i)] = z[e];
         }
     }
-    __syncwarp(gm);
 }
 
 // ------------------------------------------------------------------ row phases
@@ -538,22 +547,8 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParamsT<ty
             // continue: the spectrum of the stored chibar, then the loop as after iteration 0
             cluster_barrier<G::C>();  // peers running before their shared memory is written
             rows_forward_state<G>(cx, prm.chibar, base);
-            cluster_barrier<G::C>();
-#pragma unroll 1
-            for (int n = 0; n < prm.n_iter; ++n) {
-                column_pass<G>(cx, prm.dtab, prm.ddtab);
-                cluster_barrier<G::C>();
-                phase_dual<G>(cx, prm, base, inv_den);
-                cluster_barrier<G::C>();
-                column_pass<G>(cx, prm.dtab, prm.ddtab);
-                cluster_barrier<G::C>();
-                phase_primal<G>(cx, prm, base, n + 1 == prm.n_iter);
-                cluster_barrier<G::C>();
-            }
-            continue;
-        }
-        // zero start (pseudocode steps 2-3): chi, chibar, p, q of own rows, own spectrum
-        {
+        } else {
+            // zero start (pseudocode steps 2-3): chi, chibar, p, q of own rows, own spectrum
             const size_t o = base + (size_t)cx.crank * OWN;
             V* ptrs[5] = {reinterpret_cast<V*>(prm.chi + o), reinterpret_cast<V*>(prm.chibar + o),
                           reinterpret_cast<V*>(prm.p + o), reinterpret_cast<V*>(prm.qx + o),
@@ -565,17 +560,21 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParamsT<ty
             for (int t = threadIdx.x; t < G::SM_TBUF; t += G::NT) cx.tbuf[t] = mk<V>(Real(0), Real(0));
         }
         cluster_barrier<G::C>();
+        // half-steps: even = column pass (u-spectrum = D F chibar_n; skipped at a zero
+        // start, where it is zero) + dual phase, odd = column pass (v-spectrum = D F W p_{n+1})
+        // + primal phase.  Each phase appears once in the code.
+        const int nh = 2 * prm.n_iter;
 #pragma unroll 1
-        for (int n = 0; n < prm.n_iter; ++n) {
-            if (n > 0) {
-                column_pass<G>(cx, prm.dtab, prm.ddtab);  // u-spectrum = D F chibar_n
+        for (int h = 0; h < nh; ++h) {
+            if (h > 0 || prm.resume) {
+                column_pass<G>(cx, prm.dtab, prm.ddtab);
                 cluster_barrier<G::C>();
             }
-            phase_dual<G>(cx, prm, base, inv_den);
-            cluster_barrier<G::C>();
-            column_pass<G>(cx, prm.dtab, prm.ddtab);  // v-spectrum = D F (W p_{n+1})
-            cluster_barrier<G::C>();
-            phase_primal<G>(cx, prm, base, n + 1 == prm.n_iter);
+            if ((h & 1) == 0) {
+                phase_dual<G>(cx, prm, base, inv_den);
+            } else {
+                phase_primal<G>(cx, prm, base, h + 1 == nh);
+            }
             cluster_barrier<G::C>();
         }
     }
