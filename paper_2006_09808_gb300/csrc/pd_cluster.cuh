@@ -160,6 +160,22 @@ __device__ __forceinline__ void cluster_barrier() {
     }
 }
 
+// Split form of the cluster barrier: arrive (release) after a CTA's last write
+// of a phase, wait (acquire) before its first read of the peers' data, with
+// independent work in between.  C = 1: the wait is a CTA barrier.
+template <int C>
+__device__ __forceinline__ void cluster_arrive() {
+    if constexpr (C > 1) __cluster_barrier_arrive();
+}
+template <int C>
+__device__ __forceinline__ void cluster_wait() {
+    if constexpr (C == 1) {
+        __syncthreads();
+    } else {
+        __cluster_barrier_wait();
+    }
+}
+
 template <class G>
 struct Ctx {
     using V = typename G::V;
@@ -352,8 +368,12 @@ constexpr int kChunk = 2;
 // Phase B: u = D chibar -> dual proxes -> forward transform of W p.
 // q and p stay exactly zero wherever the 0/1 mask is zero (zero start, masked
 // increments), so W p = p and M q = q: the adjoint transform takes p as is.
+// Entered after cluster_arrive(): the first row pass waits for the peers once
+// its own-row chibar is in flight (early_cb: that row was written by this
+// thread, or by an earlier launch; not so right after the zero start).
 template <class G>
-__device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base, typename G::Real inv_den) {
+__device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base,
+                                           typename G::Real inv_den, bool early_cb) {
     using V = typename G::V;
     using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
@@ -377,9 +397,11 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
         const size_t rowoff = base + (size_t)i * W;
         const bool has_down = (i + 1 < H);
         // chibar of this row; its right neighbours come from the next lane by shuffle
+        if (pass == 0 && !early_cb) cluster_wait<G::C>();
         V cb[ER];
 #pragma unroll
         for (int e = 0; e < ER; ++e) cb[e] = __ldcg(reinterpret_cast<const V*>(cbar + rowoff + 2 * (g + TR * e)));
+        if (pass == 0 && early_cb) cluster_wait<G::C>();
         V x[ER];
         row_inverse<G>(cx, rs, i, g, gm, x);
         Real cr[ER];
@@ -433,6 +455,8 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
 
 // Phase A: v = D W p -> primal step -> over-relaxation -> forward transform of chibar.
 // G^T M q = G^T q because q vanishes outside the mask (see phase_dual).
+// Entered after cluster_arrive(): the own-row qx (written by this thread in
+// the dual phase) is loaded before the wait.
 template <class G>
 __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base,
                                              bool last) {
@@ -459,6 +483,7 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
         V qx[ER];
 #pragma unroll
         for (int e = 0; e < ER; ++e) qx[e] = __ldcg(reinterpret_cast<const V*>(qxp + rowoff + 2 * (g + TR * e)));
+        if (pass == 0) cluster_wait<G::C>();
         V x[ER];
         row_inverse<G>(cx, rs, i, g, gm, x);
         Real ql[ER];
@@ -559,24 +584,25 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParamsT<ty
                 for (int t = threadIdx.x; t < OWN / 2; t += G::NT) __stcg(ptrs[a] + t, z2);
             for (int t = threadIdx.x; t < G::SM_TBUF; t += G::NT) cx.tbuf[t] = mk<V>(Real(0), Real(0));
         }
-        cluster_barrier<G::C>();
         // half-steps: even = column pass (u-spectrum = D F chibar_n; skipped at a zero
         // start, where it is zero) + dual phase, odd = column pass (v-spectrum = D F W p_{n+1})
-        // + primal phase.  Each phase appears once in the code.
+        // + primal phase.  Each phase appears once in the code.  A row phase is
+        // entered after cluster_arrive() and waits inside, after its own-row loads.
         const int nh = 2 * prm.n_iter;
 #pragma unroll 1
         for (int h = 0; h < nh; ++h) {
             if (h > 0 || prm.resume) {
-                column_pass<G>(cx, prm.dtab, prm.ddtab);
                 cluster_barrier<G::C>();
+                column_pass<G>(cx, prm.dtab, prm.ddtab);
             }
+            cluster_arrive<G::C>();
             if ((h & 1) == 0) {
-                phase_dual<G>(cx, prm, base, inv_den);
+                phase_dual<G>(cx, prm, base, inv_den, h > 0 || prm.resume);
             } else {
                 phase_primal<G>(cx, prm, base, h + 1 == nh);
             }
-            cluster_barrier<G::C>();
         }
+        cluster_barrier<G::C>();  // the last phase's gathers done before the next slice writes
     }
 }
 
