@@ -135,6 +135,23 @@ PCS_API pcs_status pcs_solve_slices(pcs_ctx *ctx, const float *field, const unsi
                             pcs_slice_report *rep);
 
 /*
+ * pcs_solve_slices with a non-binary data weighting.  Eq. (1) weights the
+ * data residual by a matrix W and restricts the TV term by a mask M
+ * (Sec. II.A); pcs_solve_slices takes W = M = mask.  Here weight is W
+ * (device float32 [S][H][W], 16-byte aligned, values in [0, 1] so that the
+ * full-mask step sizes stay valid) and mask is M.  The dual data step becomes
+ * p <- (p + sigma W (u - dB)) / (1 + sigma/lambda) and the adjoint transform
+ * takes W p.  With weight equal to the 0/1 mask the result is bit-identical
+ * to pcs_solve_slices.  rep (optional) reports the weighted objective, gap,
+ * stationarity and residual ||W (D chi - dB)||.  Runs on the streaming
+ * kernel: a context created for the resident kernel returns PCS_EUNSUPPORTED.
+ * Errors as pcs_solve_slices; PCS_EINVAL if weight is NULL or misaligned.
+ */
+PCS_API pcs_status pcs_solve_slices_weighted(pcs_ctx *ctx, const float *field, const unsigned char *mask,
+                                             const float *weight, int S, double lambda, double tau,
+                                             double sigma, int n_iter, float *chi_out, pcs_slice_report *rep);
+
+/*
  * Same as pcs_solve_slices, but field, mask and chi_out are HOST buffers
  * (pinned memory gives full copy bandwidth).  Copies the inputs to
  * library-owned device staging buffers, solves, copies chi back and

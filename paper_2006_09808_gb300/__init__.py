@@ -149,6 +149,7 @@ def load_library(path: str = LIB_PATH):
         "pcs_set_stream": (i, [vp, vp]),
         "pcs_solve_slices": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_host": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
+        "pcs_solve_slices_weighted": (i, [vp, vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_report": (i, [vp, vp, vp, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_monitored": (i, [vp, vp, vp, i, d, d, d, i, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
@@ -259,6 +260,21 @@ def pcs_solve_slices(ctx, field, mask, lam: float, tau: float, sigma: float, n_i
     c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
     rep = (pcs_slice_report * S)() if report and S > 0 else None
     _check(load_library().pcs_solve_slices(ctx, f, m, S, lam, tau, sigma, n_iter, c, rep), "pcs_solve_slices")
+    return [r.as_dict() for r in rep] if rep is not None else None
+
+
+def pcs_solve_slices_weighted(ctx, field, mask, weight, lam: float, tau: float, sigma: float, n_iter: int, chi_out,
+                              report=False):
+    """pcs_solve_slices with data weighting W = weight ([S][H][W] float32 CUDA tensor, values in [0, 1]);
+    mask is the TV mask M."""
+    S, H, W = field.shape
+    f = _dev_ptr(field, "float32", (S, H, W), "field")
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    w = _dev_ptr(weight, "float32", (S, H, W), "weight")
+    c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
+    rep = (pcs_slice_report * S)() if report and S > 0 else None
+    _check(load_library().pcs_solve_slices_weighted(ctx, f, m, w, S, lam, tau, sigma, n_iter, c, rep),
+           "pcs_solve_slices_weighted")
     return [r.as_dict() for r in rep] if rep is not None else None
 
 

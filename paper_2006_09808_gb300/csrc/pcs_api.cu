@@ -199,8 +199,9 @@ pcs_status validate_solve(pcs_ctx* ctx, const void* field, const void* mask, int
 pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
                         double tau, double sigma, int n_iter, float* chi_out,
                         const float* inv_den_slice = nullptr, const pcs::KernelEntry* entry = nullptr,
-                        int ncl_override = 0, int resume = 0, const int* active = nullptr) {
-    if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out))
+                        int ncl_override = 0, int resume = 0, const int* active = nullptr,
+                        const float* weight = nullptr) {
+    if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out) || !aligned16(weight))
         return fail(PCS_EINVAL, "device buffers must be 16-byte aligned");
     pcs::PDParams prm;
     std::memset(&prm, 0, sizeof(prm));  // padding too: the graph cache compares whole structs
@@ -223,6 +224,7 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     prm.active = active;
     prm.resume = resume;
     prm.tv_iso = ctx->opt.tv;
+    prm.weight = weight;
     int ncl = ncl_override > 0 ? ncl_override : ctx->max_clusters;
     if (ctx->opt.max_clusters > 0 && ctx->opt.max_clusters < ncl) ncl = ctx->opt.max_clusters;
     if (ncl > S) ncl = S;
@@ -310,7 +312,7 @@ namespace pcs {
 // Objective, Fenchel-Young gap, stationarity and residual of every slice at
 // (chi, p, q) where p, q are the context's dual state of the last solve.
 pcs_status ctx_report(pcs_ctx* c, const float* field, const unsigned char* mask, int S, double lambda,
-                      const float* chi, pcs_slice_report* rep) {
+                      const float* chi, pcs_slice_report* rep, const float* weight) {
     pcs_status st = ensure_aux(c);
     if (st != PCS_OK) return st;
     AuxParams a = aux_params(c, S);
@@ -319,6 +321,7 @@ pcs_status ctx_report(pcs_ctx* c, const float* field, const unsigned char* mask,
     a.chi = chi;
     a.lam = (float)lambda;
     a.tv_iso = c->opt.tv;
+    a.weight = weight;
     PCS_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
     PCS_CUDA(c->entry->launch_report(a, aux_clusters(c, S), c->stream), "launch of the report kernel");
     const int C = c->entry->C;
@@ -442,7 +445,23 @@ pcs_status pcs_solve_slices(pcs_ctx* ctx, const float* field, const unsigned cha
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
     st = launch_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || !rep) return st;
-    return pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, rep);
+    return pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, rep, nullptr);
+}
+
+pcs_status pcs_solve_slices_weighted(pcs_ctx* ctx, const float* field, const unsigned char* mask,
+                                     const float* weight, int S, double lambda, double tau, double sigma,
+                                     int n_iter, float* chi_out, pcs_slice_report* rep) {
+    pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
+    if (st != PCS_OK || S == 0) return st;
+    if (!weight) return fail(PCS_EINVAL, "weight is NULL");
+    if (ctx->entry->resident)
+        return fail(PCS_EUNSUPPORTED, "weighted solves run on the streaming kernel (create the context with kernel 1)");
+    std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
+    st = launch_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out, nullptr, nullptr, 0, 0, nullptr,
+                      weight);
+    if (st != PCS_OK || !rep) return st;
+    return pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, rep, weight);
 }
 
 pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const unsigned char* mask_host, int S,
@@ -468,7 +487,7 @@ pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const un
     PCS_CUDA(cudaMemcpyAsync(chi_out_host, ctx->st_chi, m * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
              "D2H chi");
     PCS_CUDA(cudaStreamSynchronize(ctx->stream), "stream sync");
-    if (rep) return pcs::ctx_report(ctx, ctx->st_field, ctx->st_mask, S, lambda, ctx->st_chi, rep);
+    if (rep) return pcs::ctx_report(ctx, ctx->st_field, ctx->st_mask, S, lambda, ctx->st_chi, rep, nullptr);
     return PCS_OK;
 }
 
@@ -479,7 +498,7 @@ pcs_status pcs_report(pcs_ctx* ctx, const float* field, const unsigned char* mas
     if (S == 0) return PCS_OK;
     if (!field || !mask || !chi || !rep) return fail(PCS_EINVAL, "NULL argument");
     if (!(lambda > 0.0)) return fail(PCS_EINVAL, "lambda must be > 0");
-    return pcs::ctx_report(ctx, field, mask, S, lambda, chi, rep);
+    return pcs::ctx_report(ctx, field, mask, S, lambda, chi, rep, nullptr);
 }
 
 pcs_status pcs_opnorm(pcs_ctx* ctx, const unsigned char* mask, int S, int power_iters, double* L_out) {
@@ -526,7 +545,7 @@ pcs_status pcs_solve_slices_monitored(pcs_ctx* ctx, const float* field, const un
             if (act[s]) iters[s] = done;
         // FP64 diagnostics of every slice (frozen slices keep their last state)
         std::vector<pcs_slice_report> r(S);
-        st = pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, r.data());
+        st = pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, r.data(), nullptr);
         if (st != PCS_OK) return st;
         int n_active = 0;
         for (int s = 0; s < S; ++s) {

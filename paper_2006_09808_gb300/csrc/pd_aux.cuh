@@ -35,6 +35,7 @@ struct AuxParams {
     float lam;
     int iters;
     int tv_iso;
+    const float* weight;  // NULL: W = mask
 };
 
 constexpr int kReportSums = 5;  // data_sq, tv_l1, fy1_sq, fy2, stat_sq
@@ -132,13 +133,19 @@ __global__ void __launch_bounds__(G::NT, 1) aux_report_kernel(AuxParams prm) {
                 const float2 qx = __ldcg(reinterpret_cast<const float2*>(prm.qx + o));
                 const float2 qy = __ldcg(reinterpret_cast<const float2*>(prm.qy + o));
                 const float m[2] = {(float)mk.x, (float)mk.y};
+                float w[2] = {m[0], m[1]};
+                if (prm.weight) {
+                    const float2 wv = __ldg(reinterpret_cast<const float2*>(prm.weight + o));
+                    w[0] = wv.x;
+                    w[1] = wv.y;
+                }
                 const float u[2] = {x[e].x, x[e].y}, ff[2] = {f.x, f.y}, pp[2] = {p.x, p.y};
                 const float gx[2] = {m[0] * (c.y - c.x), m[1] * (cr - c.y)};
                 const float gy[2] = {m[0] * (cd.x - c.x), m[1] * (cd.y - c.y)};
                 const float qxs[2] = {qx.x, qx.y}, qys[2] = {qy.x, qy.y};
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
-                    const double r = (double)m[t] * ((double)u[t] - (double)ff[t]);
+                    const double r = (double)w[t] * ((double)u[t] - (double)ff[t]);
                     acc[0] += r * r;
                     const double gxd = gx[t], gyd = gy[t];
                     const double tvn = prm.tv_iso ? sqrt(gxd * gxd + gyd * gyd) : fabs(gxd) + fabs(gyd);
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(G::NT, 1) aux_report_kernel(AuxParams prm) {
                     acc[2] += d1 * d1;
                     acc[3] += tvn - ((double)qxs[t] * gxd + (double)qys[t] * gyd);
                 }
-                x[e] = make_float2(m[0] * p.x, m[1] * p.y);
+                x[e] = make_float2(w[0] * p.x, w[1] * p.y);
             }
             row_forward<G>(cx, rs, i, g, gm, x);
         }

@@ -70,6 +70,7 @@ struct PDParamsT {
     const int* active;          // NULL, or per-slice flag [S]: 0 = leave this slice untouched
     int resume;                 // 0: zero start; 1: continue from chi (chi_out), chibar, p, q
     int tv_iso;                 // 0: componentwise clamp (anisotropic TV); 1: unit-disc projection (isotropic)
+    const Real* weight;         // NULL: data weighting W = mask; else W [S][H][W] (values in [0, 1])
 };
 
 // Dual TV prox of one pixel: v = q + sigma M G chibar; clamp each component, or
@@ -366,8 +367,9 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
 constexpr int kChunk = 2;
 
 // Phase B: u = D chibar -> dual proxes -> forward transform of W p.
-// q and p stay exactly zero wherever the 0/1 mask is zero (zero start, masked
-// increments), so W p = p and M q = q: the adjoint transform takes p as is.
+// q stays exactly zero wherever the 0/1 mask M is zero (zero start, masked
+// increments), so M q = q; p likewise wherever W is zero.  With W = mask the
+// product W p equals p bit for bit.
 // Entered after cluster_arrive(): the first row pass waits for the peers once
 // its own-row chibar is in flight (early_cb: that row was written by this
 // thread, or by an earlier launch; not so right after the zero start).
@@ -430,11 +432,17 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
                 Real right = cr[e];
                 if (g == TR - 1) right = (e + 1 < ER) ? cr[e + 1] : cb[e].y;
                 const Real m0 = mk[c].x ? Real(1) : Real(0), m1 = mk[c].y ? Real(1) : Real(0);
+                Real w0 = m0, w1 = m1;
+                if (prm.weight) {  // non-binary W (weighted solves only)
+                    const V wv = __ldg(reinterpret_cast<const V*>(prm.weight + o));
+                    w0 = wv.x;
+                    w1 = wv.y;
+                }
                 const V u = x[e];
-                // dual data prox (W = mask, W dB formed on the fly)
+                // dual data prox (W dB formed on the fly)
                 V pn;
-                pn.x = (p[c].x + sigma * (m0 * (u.x - f[c].x))) * inv_den;
-                pn.y = (p[c].y + sigma * (m1 * (u.y - f[c].y))) * inv_den;
+                pn.x = (p[c].x + sigma * (w0 * (u.x - f[c].x))) * inv_den;
+                pn.y = (p[c].y + sigma * (w1 * (u.y - f[c].y))) * inv_den;
                 // dual TV prox (forward differences of chibar, Neumann boundary)
                 V qxn, qyn;
                 qxn.x = qx[c].x + sigma * m0 * (cb[e].y - cb[e].x);
@@ -446,7 +454,8 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
                 __stcg(reinterpret_cast<V*>(pp + o), pn);
                 __stcg(reinterpret_cast<V*>(qxp + o), qxn);
                 __stcg(reinterpret_cast<V*>(qyp + o), qyn);
-                x[e] = pn;  // W p = p: input of the adjoint transform
+                x[e].x = w0 * pn.x;  // W p: input of the adjoint transform
+                x[e].y = w1 * pn.y;
             }
         }
         row_forward<G>(cx, rs, i, g, gm, x);

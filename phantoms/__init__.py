@@ -19,6 +19,7 @@ from .generator import (  # noqa: F401
     config1,
     volume,
     config2,
+    magnitude_weight,
     config4_volumes,
     config5_arrivals,
 )

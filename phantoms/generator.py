@@ -225,6 +225,23 @@ def volume(
     )
 
 
+def magnitude_weight(mask: np.ndarray, seed: int, floor: float = 0.2) -> np.ndarray:
+    """A magnitude-like data weighting W in [floor, 1] inside the mask, 0 outside.
+
+    Smooth image intensity stand-in (the paper's W comes from the scanner
+    magnitude, which is not available): white noise from
+    ``default_rng(seed)`` low-passed by a Gaussian (sigma 6 px in-plane, 1
+    slice), mapped linearly onto [floor, 1] over the mask, times the mask.
+    float32 [S][H][W].
+    """
+    rng = np.random.default_rng(seed)
+    m = np.asarray(mask) != 0
+    sm = ndimage.gaussian_filter(rng.standard_normal(m.shape), sigma=(1.0, 6.0, 6.0))
+    lo, hi = sm[m].min(), sm[m].max()
+    w = floor + (1.0 - floor) * (sm - lo) / max(hi - lo, 1e-30)
+    return np.ascontiguousarray(np.where(m, w, 0.0), dtype=np.float32)
+
+
 def config2(S: int = 64) -> SliceProblem:
     """256x256x64 volume, six seeds/needles, lambda = 5e-4, 500 iterations, seed 0."""
     return volume(256, 256, S, seed=0, lam=5e-4, n_iter=500, name=f"cfg2-256x256x{S}")
