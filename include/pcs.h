@@ -194,6 +194,33 @@ PCS_API pcs_status pcs_solve_slices_f64(const double *field, const unsigned char
                                         double lambda, double tau, double sigma, int n_iter, double *chi_out,
                                         int b0_axis, void *cuda_stream);
 
+/* ---------------------------------------------------------------- 3-D variant */
+
+/*
+ * Eq. (1) with the gradient G in all three dimensions and the 3-D dipole
+ * convolution of the whole volume (Sec. II.A; the per-slice solver above
+ * reads G as 2-D and solves slices independently).  The volume [S][H][W] is
+ * one unknown: D(k) = 1/3 - kz^2/|k|^2 with B0 along z (the slice axis),
+ * periodic on the S x H x W grid, isotropic voxels; G = forward differences
+ * along x, y, z with a Neumann boundary; W = M = mask.  The Sec. II.A
+ * iteration runs n_iter times from the zero start (tau, sigma as for
+ * pcs_solve_slices; ||K|| <= sqrt(4/9 + 12) for any 0/1 mask, so
+ * tau = sigma = 1/3.53 is always valid).  tv: 0 anisotropic (clamp of each of
+ * the three components), 1 isotropic (projection onto the unit ball).
+ * field, chi_out: device float32 [S][H][W]; mask: device uint8; 16-byte
+ * aligned; chi_out must not alias field.  Allocates its scratch (6 floats and
+ * a half spectrum per voxel), frees it and synchronises cuda_stream before
+ * returning.  Shapes: H = W in {64, 128, 256}, S in {32, 64} (and 128 for
+ * H >= 128); others PCS_EUNSUPPORTED.  Errors: PCS_EINVAL for bad arguments,
+ * PCS_ECUDA for CUDA failures.
+ */
+PCS_API pcs_status pcs_solve_volume_3d(const float *field, const unsigned char *mask, int S, int H, int W,
+                                       double lambda, double tau, double sigma, int n_iter, int tv,
+                                       float *chi_out, void *cuda_stream);
+
+/* 1 if pcs_solve_volume_3d has kernels for an S x H x W volume, else 0. */
+PCS_API int pcs_supported_volume_3d(int S, int H, int W);
+
 /* ---------------------------------------------------------------- uneven batches */
 
 typedef struct pcs_batch pcs_batch; /* opaque */

@@ -150,6 +150,8 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_slices": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_host": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_weighted": (i, [vp, vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
+        "pcs_solve_volume_3d": (i, [vp, vp, i, i, i, d, d, d, i, i, vp, vp]),
+        "pcs_supported_volume_3d": (i, [i, i, i]),
         "pcs_report": (i, [vp, vp, vp, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_monitored": (i, [vp, vp, vp, i, d, d, d, i, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
@@ -276,6 +278,24 @@ def pcs_solve_slices_weighted(ctx, field, mask, weight, lam: float, tau: float, 
     _check(load_library().pcs_solve_slices_weighted(ctx, f, m, w, S, lam, tau, sigma, n_iter, c, rep),
            "pcs_solve_slices_weighted")
     return [r.as_dict() for r in rep] if rep is not None else None
+
+
+def pcs_solve_volume_3d(field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, tv: int = 0,
+                        stream=None):
+    """3-D solve of one volume (field/mask/chi_out: [S][H][W] float32/uint8/float32 CUDA tensors)."""
+    import torch
+
+    S, H, W = field.shape
+    f = _dev_ptr(field, "float32", (S, H, W), "field")
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(load_library().pcs_solve_volume_3d(f, m, S, H, W, lam, tau, sigma, n_iter, tv, c, ctypes.c_void_p(st)),
+           "pcs_solve_volume_3d")
+
+
+def pcs_supported_volume_3d(S: int, H: int, W: int) -> bool:
+    return bool(load_library().pcs_supported_volume_3d(S, H, W))
 
 
 def pcs_solve_slices_host(ctx, field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, report=False):

@@ -1,0 +1,182 @@
+// pd_3d.cu -- instances and the C-ABI entry point of the 3-D variant
+// (pcs_solve_volume_3d; kernels in pd_3d.cuh).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/pcs.h"
+#include "pd_3d.cuh"
+#include "pd_launch.cuh"
+
+namespace pcs {
+void build_twiddles(int n, std::vector<float2>& tw);
+pcs_status set_last_error(pcs_status st, const char* msg);
+}  // namespace pcs
+
+namespace {
+
+using pcs::Geo;
+using pcs::GeoZ;
+using pcs::P3Params;
+
+struct Slice3Entry {
+    int H, W;
+    size_t smem;
+    cudaError_t (*prepare)(int* max_clusters);
+    cudaError_t (*launch)(const P3Params& a, int n_clusters, cudaStream_t st);
+};
+
+template <class G>
+cudaError_t prepare3(int* mc) {
+    return pcs::prepare_cluster<G>(pcs::pd3_slice_kernel<G>, G::SMEM_BYTES, mc);
+}
+template <class G>
+cudaError_t launch3(const P3Params& a, int ncl, cudaStream_t st) {
+    return pcs::launch_cluster<G>(pcs::pd3_slice_kernel<G>, a, G::SMEM_BYTES, ncl, st);
+}
+template <class G>
+constexpr Slice3Entry slice3_entry() {
+    return Slice3Entry{G::H, G::W, G::SMEM_BYTES, &prepare3<G>, &launch3<G>};
+}
+
+const Slice3Entry k_slice3[] = {
+    slice3_entry<Geo<64, 64, 1>>(),
+    slice3_entry<Geo<128, 128, 2>>(),
+    slice3_entry<Geo<256, 256, 4, 2>>(),
+};
+
+struct Z3Entry {
+    int NZ, H, W;
+    cudaError_t (*launch)(float2* spec, const float2* twid, int ntw, cudaStream_t st);
+};
+
+template <int NZ, int H, int W>
+cudaError_t launch_z(float2* spec, const float2* twid, int ntw, cudaStream_t st) {
+    using GZ = GeoZ<NZ, H, W>;
+    const dim3 grid(GZ::M + 1, H / GZ::TY);
+    pcs::pd3_z_kernel<GZ, NZ, H, W><<<grid, 256, GZ::SMEM_BYTES, st>>>(spec, twid, ntw);
+    return cudaGetLastError();
+}
+
+const Z3Entry k_z3[] = {
+    {32, 64, 64, &launch_z<32, 64, 64>},      {64, 64, 64, &launch_z<64, 64, 64>},
+    {32, 128, 128, &launch_z<32, 128, 128>},  {64, 128, 128, &launch_z<64, 128, 128>},
+    {128, 128, 128, &launch_z<128, 128, 128>}, {32, 256, 256, &launch_z<32, 256, 256>},
+    {64, 256, 256, &launch_z<64, 256, 256>},  {128, 256, 256, &launch_z<128, 256, 256>},
+};
+
+pcs_status fail3(pcs_status st, const char* what, cudaError_t e = cudaSuccess) {
+    char buf[256];
+    if (e != cudaSuccess) {
+        snprintf(buf, sizeof(buf), "pcs_solve_volume_3d: %s: %s", what, cudaGetErrorString(e));
+    } else {
+        snprintf(buf, sizeof(buf), "pcs_solve_volume_3d: %s", what);
+    }
+    return pcs::set_last_error(st, buf);
+}
+
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int pcs_supported_volume_3d(int S, int H, int W) {
+    bool slice = false, z = false;
+    for (const auto& e : k_slice3) slice = slice || (e.H == H && e.W == W);
+    for (const auto& e : k_z3) z = z || (e.NZ == S && e.H == H && e.W == W);
+    return (slice && z) ? 1 : 0;
+}
+
+pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, int S, int H, int W, double lambda,
+                               double tau, double sigma, int n_iter, int tv, float* chi_out, void* cuda_stream) {
+    if (!field || !mask || !chi_out) return fail3(PCS_EINVAL, "NULL argument");
+    if (!(lambda > 0.0) || !(tau > 0.0) || !(sigma > 0.0)) return fail3(PCS_EINVAL, "lambda, tau, sigma must be > 0");
+    if (n_iter < 0) return fail3(PCS_EINVAL, "n_iter must be >= 0");
+    if (tv != 0 && tv != 1) return fail3(PCS_EINVAL, "tv must be 0 or 1");
+    if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out))
+        return fail3(PCS_EINVAL, "device buffers must be 16-byte aligned");
+    if (field == chi_out) return fail3(PCS_EINVAL, "chi_out must not alias field");
+    const Slice3Entry* se = nullptr;
+    const Z3Entry* ze = nullptr;
+    for (const auto& e : k_slice3)
+        if (e.H == H && e.W == W) se = &e;
+    for (const auto& e : k_z3)
+        if (e.NZ == S && e.H == H && e.W == W) ze = &e;
+    if (!se || !ze) return fail3(PCS_EUNSUPPORTED, "no 3-D kernel for this volume shape");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t n = (size_t)S * H * W;
+    const size_t nspec = (size_t)S * (W / 2 + 1) * H;
+    const int ntw = H > W ? H : W;
+    std::vector<float2> tw;
+    pcs::build_twiddles(ntw, tw);
+
+    float* state = nullptr;  // chibar, p, qx, qy, qz
+    float2* spec = nullptr;
+    float2* twid = nullptr;
+    cudaError_t e;
+    int ncl = 0;
+    pcs_status ret = PCS_OK;
+    if ((e = cudaMalloc(&state, 5 * n * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&spec, nspec * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&twid, tw.size() * sizeof(float2))) != cudaSuccess) {
+        ret = fail3(PCS_ECUDA, "cudaMalloc", e);
+    } else if ((e = cudaMemcpyAsync(twid, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st)) !=
+                   cudaSuccess ||
+               (e = cudaMemsetAsync(state, 0, 5 * n * sizeof(float), st)) != cudaSuccess ||
+               (e = cudaMemsetAsync(chi_out, 0, n * sizeof(float), st)) != cudaSuccess ||
+               (e = se->prepare(&ncl)) != cudaSuccess) {
+        ret = fail3(PCS_ECUDA, "set-up", e);
+    } else {
+        P3Params a;
+        std::memset(&a, 0, sizeof(a));
+        a.pd.field = field;
+        a.pd.mask = mask;
+        a.pd.chi = chi_out;
+        a.pd.chibar = state;
+        a.pd.p = state + n;
+        a.pd.qx = state + 2 * n;
+        a.pd.qy = state + 3 * n;
+        a.pd.qz = state + 4 * n;
+        a.pd.twid = twid;
+        a.pd.S = S;
+        a.pd.n_iter = n_iter;
+        a.pd.sigma = (float)sigma;
+        a.pd.tau = (float)tau;
+        a.pd.inv_den = (float)(1.0 / (1.0 + sigma / lambda));
+        a.pd.tv_iso = tv;
+        a.spec = spec;
+        if (ncl > S) ncl = S;
+        if (ncl < 1) ncl = 1;
+        // iteration n: dual step from the spectrum of chibar_n (zero at n = 0), z pass,
+        // primal step, z pass (the spectrum of chibar_{n+1}; not after the last)
+        for (int it = 0; it < n_iter && ret == PCS_OK; ++it) {
+            a.phase = 0;
+            a.load = it > 0;
+            a.store = 1;
+            if ((e = se->launch(a, ncl, st)) != cudaSuccess || (e = ze->launch(spec, twid, ntw, st)) != cudaSuccess) {
+                ret = fail3(PCS_ECUDA, "launch", e);
+                break;
+            }
+            a.phase = 1;
+            a.load = 1;
+            a.store = it + 1 < n_iter;
+            if ((e = se->launch(a, ncl, st)) != cudaSuccess ||
+                (a.store && (e = ze->launch(spec, twid, ntw, st)) != cudaSuccess)) {
+                ret = fail3(PCS_ECUDA, "launch", e);
+                break;
+            }
+        }
+    }
+    // synchronous: the call owns its scratch
+    cudaError_t se2 = cudaStreamSynchronize(st);
+    if (ret == PCS_OK && se2 != cudaSuccess) ret = fail3(PCS_ECUDA, "stream sync", se2);
+    cudaFree(state);
+    cudaFree(spec);
+    cudaFree(twid);
+    return ret;
+}
+
+}  // extern "C"

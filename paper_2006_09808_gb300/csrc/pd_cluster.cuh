@@ -71,10 +71,26 @@ struct PDParamsT {
     int resume;                 // 0: zero start; 1: continue from chi (chi_out), chibar, p, q
     int tv_iso;                 // 0: componentwise clamp (anisotropic TV); 1: unit-disc projection (isotropic)
     const Real* weight;         // NULL: data weighting W = mask; else W [S][H][W] (values in [0, 1])
+    Real* qz;                   // 3-D variant only: z component of q [S][H][W]
 };
 
 // Dual TV prox of one pixel: v = q + sigma M G chibar; clamp each component, or
 // project (vx, vy) onto the unit disc.
+// Three components (3-D variant).
+template <class Real>
+__device__ __forceinline__ void tv_prox3(Real& vx, Real& vy, Real& vz, int iso) {
+    if (iso) {
+        const Real n = fmax(Real(1), sqrt(vx * vx + vy * vy + vz * vz));
+        vx = vx / n;
+        vy = vy / n;
+        vz = vz / n;
+    } else {
+        vx = fmin(Real(1), fmax(Real(-1), vx));
+        vy = fmin(Real(1), fmax(Real(-1), vy));
+        vz = fmin(Real(1), fmax(Real(-1), vz));
+    }
+}
+
 template <class Real>
 __device__ __forceinline__ void tv_prox(Real& vx, Real& vy, int iso) {
     if (iso) {
@@ -373,9 +389,11 @@ constexpr int kChunk = 2;
 // Entered after cluster_arrive(): the first row pass waits for the peers once
 // its own-row chibar is in flight (early_cb: that row was written by this
 // thread, or by an earlier launch; not so right after the zero start).
-template <class G>
+// Z3 (3-D variant): q also has a z component, updated from chibar of the next
+// slice (zero difference on the last slice); s is the slice of base.
+template <class G, bool Z3 = false>
 __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base,
-                                           typename G::Real inv_den, bool early_cb) {
+                                           typename G::Real inv_den, bool early_cb, int s = 0) {
     using V = typename G::V;
     using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
@@ -449,8 +467,21 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
                 qxn.y = qx[c].y + sigma * m1 * (right - cb[e].y);
                 qyn.x = qy[c].x + sigma * m0 * (cd[c].x - cb[e].x);
                 qyn.y = qy[c].y + sigma * m1 * (cd[c].y - cb[e].y);
-                tv_prox(qxn.x, qyn.x, prm.tv_iso);
-                tv_prox(qxn.y, qyn.y, prm.tv_iso);
+                if constexpr (Z3) {
+                    constexpr size_t SL = (size_t)G::H * G::W;
+                    V qzn = __ldcg(reinterpret_cast<const V*>(prm.qz + o));
+                    if (s + 1 < prm.S) {
+                        const V cz = __ldcg(reinterpret_cast<const V*>(cbar + o + SL));
+                        qzn.x += sigma * m0 * (cz.x - cb[e].x);
+                        qzn.y += sigma * m1 * (cz.y - cb[e].y);
+                    }
+                    tv_prox3(qxn.x, qyn.x, qzn.x, prm.tv_iso);
+                    tv_prox3(qxn.y, qyn.y, qzn.y, prm.tv_iso);
+                    __stcg(reinterpret_cast<V*>(prm.qz + o), qzn);
+                } else {
+                    tv_prox(qxn.x, qyn.x, prm.tv_iso);
+                    tv_prox(qxn.y, qyn.y, prm.tv_iso);
+                }
                 __stcg(reinterpret_cast<V*>(pp + o), pn);
                 __stcg(reinterpret_cast<V*>(qxp + o), qxn);
                 __stcg(reinterpret_cast<V*>(qyp + o), qyn);
@@ -466,9 +497,11 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
 // G^T M q = G^T q because q vanishes outside the mask (see phase_dual).
 // Entered after cluster_arrive(): the own-row qx (written by this thread in
 // the dual phase) is loaded before the wait.
-template <class G>
+// Z3 (3-D variant): G^T also takes the z differences, qz[s-1] - qz[s] with the
+// same boundary rule as the rows.
+template <class G, bool Z3 = false>
 __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base,
-                                             bool last) {
+                                             bool last, int s = 0) {
     using V = typename G::V;
     using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
@@ -520,8 +553,16 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
                 const Real a1r = (j0 + 2 < W) ? qx[e].y : Real(0);
                 const Real b0 = has_down ? qy[c].x : Real(0);
                 const Real b1 = has_down ? qy[c].y : Real(0);
-                const Real d0 = (al - qx[e].x) + (qu[c].x - b0);
-                const Real d1 = (qx[e].x - a1r) + (qu[c].y - b1);
+                Real d0 = (al - qx[e].x) + (qu[c].x - b0);
+                Real d1 = (qx[e].x - a1r) + (qu[c].y - b1);
+                if constexpr (Z3) {
+                    constexpr size_t SL = (size_t)G::H * G::W;
+                    V zc = mk<V>(Real(0), Real(0)), zp = mk<V>(Real(0), Real(0));
+                    if (s + 1 < prm.S) zc = __ldcg(reinterpret_cast<const V*>(prm.qz + o));
+                    if (s > 0) zp = __ldcg(reinterpret_cast<const V*>(prm.qz + o - SL));
+                    d0 += zp.x - zc.x;
+                    d1 += zp.y - zc.y;
+                }
                 V cn;
                 cn.x = chi[c].x - tau * v.x - tau * d0;
                 cn.y = chi[c].y - tau * v.y - tau * d1;

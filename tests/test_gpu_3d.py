@@ -1,0 +1,94 @@
+"""3-D variant (pcs_solve_volume_3d) against the FP64 3-D oracle.
+
+The volume is one unknown (slices coupled through the 3-D dipole convolution
+and the z differences), so every parity case runs the oracle on the whole
+volume.  tau = sigma = 1/sqrt(4/9 + 12), a valid step for every 0/1 mask
+(||D|| <= 2/3, ||G||^2 <= 12), the same on both sides.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2006_09808_gb300 as pcs  # noqa: E402
+import phantoms  # noqa: E402
+from oracle import pd_oracle_3d as O3  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+STEP = 1.0 / math.sqrt(4.0 / 9.0 + 12.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_09808_gb300 import build
+
+    build.build()
+    pcs.load_library()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu3(field, mask, lam, n_iter, tv=0):
+    f = torch.from_numpy(np.ascontiguousarray(field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint8)).cuda()
+    chi = torch.full_like(f, float("nan"))
+    pcs.pcs_solve_volume_3d(f, m, lam, STEP, STEP, n_iter, chi, tv=tv)
+    torch.cuda.synchronize()
+    return chi.cpu().numpy()
+
+
+@pytest.mark.parametrize(
+    "S,H,n_iter,lam,tv",
+    [(32, 64, 100, 1.0, 0), (32, 64, 100, 1.0, 1), (64, 64, 60, 1e-3, 0), (32, 128, 50, 1.0, 0)],
+)
+def test_parity_3d(S, H, n_iter, lam, tv):
+    pb = phantoms.volume(H, H, S, seed=51, lam=lam, n_iter=n_iter)
+    ref = O3.pd_solve_3d(pb.field.astype(np.float64), pb.mask, lam, STEP, STEP, n_iter, tv="iso" if tv else "aniso")
+    got = gpu3(pb.field, pb.mask, lam, n_iter, tv)
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, ref) <= TOL
+    # per slice as well (the top and bottom slices see the z boundary)
+    for s in (0, S // 2, S - 1):
+        assert rel_l2(got[s], ref[s]) <= 10 * TOL, s
+
+
+def test_parity_3d_full_size_volume():
+    """256 x 256 x 64, the bench volume, 20 iterations against the whole-volume oracle."""
+    pb = phantoms.config2()
+    n = 20
+    ref = O3.pd_solve_3d(pb.field.astype(np.float64), pb.mask, pb.lam, STEP, STEP, n)
+    got = gpu3(pb.field, pb.mask, pb.lam, n)
+    assert rel_l2(got, ref) <= TOL
+    m = pb.mask.astype(bool)
+    assert rel_l2(got[m], ref[m]) <= TOL
+
+
+def test_3d_edge_cases_and_errors():
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal((32, 64, 64)).astype(np.float32)
+    ones = np.ones_like(f, dtype=np.uint8)
+    assert np.all(gpu3(f, ones, 1.0, 0) == 0)  # n_iter = 0
+    assert np.all(gpu3(f, np.zeros_like(ones), 1.0, 20) == 0)  # empty mask
+    one = gpu3(f, ones, 1.0, 1)
+    assert rel_l2(one, O3.pd_solve_3d(f.astype(np.float64), ones, 1.0, STEP, STEP, 1)) <= 1e-6
+    assert pcs.pcs_supported_volume_3d(64, 256, 256) and not pcs.pcs_supported_volume_3d(48, 256, 256)
+    bad = torch.zeros((48, 64, 64), device="cuda")
+    with pytest.raises(pcs.PcsError) as ei:
+        pcs.pcs_solve_volume_3d(bad, torch.ones((48, 64, 64), dtype=torch.uint8, device="cuda"), 1.0, STEP, STEP, 5,
+                                torch.empty_like(bad))
+    assert ei.value.status == pcs.PCS_EUNSUPPORTED
+    g = torch.zeros((32, 64, 64), device="cuda")
+    with pytest.raises(pcs.PcsError) as ei:
+        pcs.pcs_solve_volume_3d(g, torch.ones((32, 64, 64), dtype=torch.uint8, device="cuda"), -1.0, STEP, STEP, 5,
+                                torch.empty_like(g))
+    assert ei.value.status == pcs.PCS_EINVAL
