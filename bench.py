@@ -52,9 +52,8 @@ def dist_env():
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2006_09808_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in ("fft_core.cuh", "pd_cluster.cuh", "pd_launch.cuh", "pd_256.cu"):  # the iteration kernel's files
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -355,6 +354,111 @@ def run_native(args):
     return 0
 
 
+# 3-D variant (the whole volume one unknown): state and inputs 45 B (read+write chi, p, qx, qy,
+# qz; read dB, mask) plus the half spectrum through global memory, 4 passes of (W/2+1)/W x 8 B per
+# dipole convolution (slice kernel writes, z pass reads and writes, slice kernel reads), 2 per iteration
+ALG_BYTES_3D = 45 + 2 * 4 * 8 * (W // 2 + 1) / W
+STEP_3D = 1.0 / (4.0 / 9.0 + 12.0) ** 0.5  # tau = sigma: ||K|| <= sqrt(||D||^2 + ||G||^2) for any 0/1 mask
+
+
+def run_volume3d(args):
+    """3-D variant on the same 256 x 256 x 64 volume: one pcs_solve_volume_3d call per step."""
+    import numpy as np
+    import torch
+
+    import paper_2006_09808_gb300 as pcs
+    import phantoms
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pcs.load_library()
+    pb = phantoms.volume(H, W, SLICES, seed=rank, lam=LAM, n_iter=N_ITER, name="bench3d")
+    field = torch.from_numpy(pb.field).to(dev)
+    mask = torch.from_numpy(pb.mask).to(dev)
+    chi = torch.empty_like(field)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        pcs.pcs_solve_volume_3d(field, mask, LAM, STEP_3D, STEP_3D, N_ITER, chi, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    ms_step = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    work = SLICES * H * W * N_ITER
+    # end to end: pinned host field and mask in, chi out, around the same call
+    hf = torch.from_numpy(pb.field).pin_memory()
+    hm = torch.from_numpy(pb.mask).pin_memory()
+    hc = torch.empty(pb.field.shape, dtype=torch.float32).pin_memory()
+    e2e = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        field.copy_(hf, non_blocking=True)
+        mask.copy_(hm, non_blocking=True)
+        step()
+        hc.copy_(chi, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    assert torch.equal(hc, chi.cpu())
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        hbm_peak = float(peaks["hbm_gbs"])
+        achieved = ALG_BYTES_3D * work / (ms_step * 1e-3) / 1e9
+        line = {
+            "metric": "PD voxel-iterations/s (3-D variant)",
+            "value": work / (ms_step * 1e-3),
+            "unit": "voxel-iter/s",
+            "n_gpus": 1,
+            "steps": args.steps,
+            "warmup": max(args.warmup, 3),
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "3-D: the 256x256x64 volume as one unknown (3-D G and D, B0 along z), "
+                                   "500 PD iterations, lambda=5e-4", "H": H, "W": W, "slices": SLICES,
+                       "n_iter": N_ITER, "tau_sigma": STEP_3D, "l2": "flushed between steps (256 MiB device write)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "alg_bytes_per_voxel_iter": ALG_BYTES_3D},
+            "e2e": {"value": work / (sum(e2e) / len(e2e)), "unit": "voxel-iter/s",
+                    "h2d_bytes_per_step": int(pb.field.nbytes + pb.mask.nbytes),
+                    "d2h_bytes_per_step": int(pb.field.nbytes)},
+            "gpu_launches": args.steps * (4 * N_ITER - 1),
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            from oracle import pd_oracle_3d as O3  # cpu_baseline leg only
+
+            n_it = 3
+            t0 = time.perf_counter()
+            O3.pd_solve_3d(pb.field.astype(np.float64), pb.mask, LAM, STEP_3D, STEP_3D, n_it)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": work / N_ITER * n_it / dt, "unit": "voxel-iter/s", "cores": 1,
+                                    "kind": "oracle",
+                                    "sample": f"the whole volume x {n_it} iterations ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """Serving leg: Poisson arrivals of uneven-batch-style volumes, streamed slice by slice."""
     import heapq
@@ -466,8 +570,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
     ap.add_argument("--plain-loop", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the plain per-slice GPU loop (one timed volume)")
-    ap.add_argument("--workload", choices=["volume", "serve"], default="volume",
-                    help="volume: the 256x256x64 solve (default); serve: the serving loop")
+    ap.add_argument("--workload", choices=["volume", "serve", "volume3d"], default="volume",
+                    help="volume: the 256x256x64 solve (default); serve: the serving loop; "
+                         "volume3d: the 3-D variant on the same volume")
     ap.add_argument("--requests", type=int, default=80, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
     ap.add_argument("--baseline-requests", type=int, default=20, help="serving: requests in the plain baseline")
@@ -476,6 +581,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "volume3d":
+        return run_volume3d(args)
     return run_native(args)
 
 
