@@ -10,10 +10,14 @@
 // The transform is a Stockham autosort radix-R factorisation (radices 16, 8,
 // 4, 2): each stage reads its butterfly inputs at stride N/R, applies the
 // twiddles W_{Ns R}^{r k}, a register DFT_R, and writes to the next stage's
-// natural position; the group exchanges through a padded shared-memory
-// buffer between stages.  Padding: element i lives at P(i) = i + i/16 (one
-// 8-byte word per 16), which keeps the strided stores of a stage on distinct
-// banks.
+// natural position; the group exchanges through a shared-memory buffer
+// between stages.  Swizzle: element i lives at P(i, key) = i ^ ((i/16 + key)
+// mod 16), a permutation inside each aligned block of 16 that puts the
+// strided stores of a stage (16 j + r over lanes j) and the natural-order
+// accesses (g + 16 e over lanes g) on distinct banks without padding, and
+// keeps every aligned run of 4 elements inside one 32-byte sector.  key
+// varies the pattern between buffers (columns use 4 x their index, so that 8
+// adjacent columns read at 4 adjacent rows hit every bank exactly twice).
 //
 // Twiddles come from per-stage tables in shared memory laid out [r-1][k]
 // (entry W_{Ns R}^{r k}), so the lanes of a group, which hold consecutive k,
@@ -26,7 +30,7 @@
 
 namespace pcs {
 
-__device__ __forceinline__ int P(int i) { return i + (i >> 4); }
+__device__ __forceinline__ int P(int i, int key = 0) { return i ^ (((i >> 4) + key) & 15); }
 
 // Complex vector type of a real type: float -> float2, double -> double2.
 template <class Real>
@@ -291,12 +295,14 @@ __device__ __forceinline__ void twiddle(V (&v)[R], int j, const V* __restrict__ 
     }
 }
 
-// Complex FFT of length N by a group of T lanes (lane g, group mask gm).
-// x: E = N/T elements, element g + T*e in x[e]; buf: group-private padded
-// buffer of P(N-1)+1 entries (contents destroyed); stw: StageTw<N, E> table.
+// Complex FFT of length N (a multiple of 16) by a group of T lanes (lane g,
+// group mask gm).  x: E = N/T elements, element g + T*e in x[e]; buf:
+// group-private buffer of N entries addressed through P(., key) (contents
+// destroyed); stw: StageTw<N, E> table.
 template <int N, int T, bool INV, class V>
 __device__ __forceinline__ void fft(V (&x)[N / T], V* __restrict__ buf, const V* __restrict__ stw, int g,
-                                    unsigned gm) {
+                                    unsigned gm, int key = 0) {
+    static_assert(N % 16 == 0, "swizzle blocks");
     constexpr int E = N / T;
     using PL = Plan<N, E>;
     constexpr int R1 = PL::R1, RM = PL::RM, RL = PL::RL;
@@ -315,7 +321,7 @@ __device__ __forceinline__ void fft(V (&x)[N / T], V* __restrict__ buf, const V*
             dftR<R1, INV, V>(v);
             const int j = g + b * T;
 #pragma unroll
-            for (int r = 0; r < R1; ++r) buf[P(j * R1 + r)] = v[r];
+            for (int r = 0; r < R1; ++r) buf[P(j * R1 + r, key)] = v[r];
         }
     }
     __syncwarp(gm);
@@ -328,7 +334,7 @@ __device__ __forceinline__ void fft(V (&x)[N / T], V* __restrict__ buf, const V*
         for (int b = 0; b < B; ++b) {
             const int j = g + b * T;
 #pragma unroll
-            for (int r = 0; r < RM; ++r) v[b][r] = buf[P(j + r * (N / RM))];
+            for (int r = 0; r < RM; ++r) v[b][r] = buf[P(j + r * (N / RM), key)];
         }
         __syncwarp(gm);
 #pragma unroll
@@ -339,7 +345,7 @@ __device__ __forceinline__ void fft(V (&x)[N / T], V* __restrict__ buf, const V*
             const int k = j % NS;
             const int base = (j / NS) * NS * RM + k;
 #pragma unroll
-            for (int r = 0; r < RM; ++r) buf[P(base + r * NS)] = v[b][r];
+            for (int r = 0; r < RM; ++r) buf[P(base + r * NS, key)] = v[b][r];
         }
         __syncwarp(gm);
     }
@@ -352,7 +358,7 @@ __device__ __forceinline__ void fft(V (&x)[N / T], V* __restrict__ buf, const V*
             const int j = g + b * T;
             V v[RL];
 #pragma unroll
-            for (int r = 0; r < RL; ++r) v[r] = buf[P(j + r * NS)];
+            for (int r = 0; r < RL; ++r) v[r] = buf[P(j + r * NS, key)];
             twiddle<RL, NS, INV, V>(v, j, stw + StageTw<N, E>::MID);
             dftR<RL, INV, V>(v);
 #pragma unroll

@@ -44,6 +44,7 @@ __device__ __forceinline__ void columns_in_3d(const Ctx<G>& cx, const float2* __
     for (int cl = grp; cl < G::MC; cl += G::CPP) {
         const int kx = cx.crank * G::MC + cl;
         float2* col = cx.tbuf + cl * G::HP;
+        const int key = 4 * cl;
         float2 x[EC];
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
@@ -56,9 +57,9 @@ __device__ __forceinline__ void columns_in_3d(const Ctx<G>& cx, const float2* __
                 x[e] = a;
             }
         }
-        fft<H, TC, true>(x, col, cx.stw_c, g, gm);
+        fft<H, TC, true>(x, col, cx.stw_c, g, gm, key);
 #pragma unroll
-        for (int e = 0; e < EC; ++e) col[P(g + TC * e)] = x[e];
+        for (int e = 0; e < EC; ++e) col[P(g + TC * e, key)] = x[e];
         __syncwarp(gm);
     }
 }
@@ -77,18 +78,19 @@ __device__ __forceinline__ void columns_out_3d(const Ctx<G>& cx, float2* __restr
     for (int cl = grp; cl < G::MC; cl += G::CPP) {
         const int kx = cx.crank * G::MC + cl;
         float2* col = cx.tbuf + cl * G::HP;
+        const int key = 4 * cl;
         float2 x[EC];
 #pragma unroll
-        for (int e = 0; e < EC; ++e) x[e] = col[P(g + TC * e)];
-        fft<H, TC, false>(x, col, cx.stw_c, g, gm);
+        for (int e = 0; e < EC; ++e) x[e] = col[P(g + TC * e, key)];
+        fft<H, TC, false>(x, col, cx.stw_c, g, gm, key);
         if (kx == 0) {
 #pragma unroll
-            for (int e = 0; e < EC; ++e) col[P(g + TC * e)] = x[e];
+            for (int e = 0; e < EC; ++e) col[P(g + TC * e, key)] = x[e];
             __syncwarp(gm);
 #pragma unroll
             for (int e = 0; e < EC; ++e) {
                 const int ky = g + TC * e;
-                const float2 c = x[e], cm = col[P((H - ky) % H)];
+                const float2 c = x[e], cm = col[P((H - ky) % H, key)];
                 __stcg(spec + spec_index<G>(s, 0, ky), make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y)));
                 __stcg(spec + spec_index<G>(s, M, ky), make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x)));
             }
@@ -147,7 +149,7 @@ struct GeoZ {
     static constexpr int PPW = 32 / TZ;           // pencils per warp
     static constexpr int TY = (NT / 32) * PPW;    // pencils (ky values) per CTA
     static constexpr int M = W / 2;
-    static constexpr int NP = NZ + NZ / 16 + 1;  // padded pencil buffer
+    static constexpr int NP = NZ + (TZ % 16);  // pencil buffer stride: adjacent pencils on other banks
     static constexpr size_t SMEM_BYTES = sizeof(float2) * (TY * NP + StageTw<NZ, EZ>::SIZE);
     static_assert(H % TY == 0, "ky tiles");
 };

@@ -114,9 +114,6 @@ __device__ __forceinline__ V mk(RealOf<V> a, RealOf<V> b) {
     return V{a, b};
 }
 
-constexpr int ceil_to_mod16(int v, int want) {  // smallest x >= v with x % 16 == want % 16
-    return v + ((want % 16) - (v % 16) + 16) % 16;
-}
 
 // ER_, EC_: elements per lane of the row / column transforms (0 = 16 for
 // lengths >= 128, else 8).
@@ -139,8 +136,8 @@ struct Geo {
     static constexpr int RPP = NW * (32 / TR);  // rows in flight per CTA
     static constexpr int CPP = NW * (32 / TC);  // columns in flight per CTA
     // shared-memory layout (complex units)
-    static constexpr int HP = H + H / 16 + 1;                        // column stride (odd)
-    static constexpr int MP = ceil_to_mod16(M + M / 16, TR % 16);    // row-scratch stride
+    static constexpr int HP = H;              // column stride (columns swizzled with key 4 cl)
+    static constexpr int MP = M + (TR % 16);  // row-scratch stride: adjacent groups on other banks
     static constexpr int SM_TBUF = MC * HP;
     static constexpr int SM_ROWS = RPP * MP;
     static constexpr int SM_TW = NTW;
@@ -253,10 +250,11 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const typename G::
         if (G::CPP > G::MC && cl >= G::MC) break;  // whole group idles (uniform per group)
         const int kx = cx.crank * G::MC + cl;
         V* col = cx.tbuf + cl * G::HP;
+        const int key = 4 * cl;
         V x[EC];
 #pragma unroll
-        for (int e = 0; e < EC; ++e) x[e] = col[P(g + TC * e)];
-        fft<H, TC, false>(x, col, cx.stw_c, g, gm);
+        for (int e = 0; e < EC; ++e) x[e] = col[P(g + TC * e, key)];
+        fft<H, TC, false>(x, col, cx.stw_c, g, gm, key);
         if (kx != 0) {
             const Real* d = dtab + (size_t)kx * H;
 #pragma unroll
@@ -264,24 +262,33 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const typename G::
         } else {
             // packed DC / Nyquist column: pair ky with -ky
 #pragma unroll
-            for (int e = 0; e < EC; ++e) col[P(g + TC * e)] = x[e];
+            for (int e = 0; e < EC; ++e) col[P(g + TC * e, key)] = x[e];
             __syncwarp(gm);
 #pragma unroll
             for (int e = 0; e < EC; ++e) {
                 const int ky = g + TC * e;
-                const V ym = col[P((H - ky) % H)];
+                const V ym = col[P((H - ky) % H, key)];
                 const Real dm = __ldg(dtab + ky), dd = __ldg(ddtab + ky);
                 x[e] = mk<V>(fma(dm, x[e].x, dd * ym.x), fma(dm, x[e].y, -dd * ym.y));
             }
         }
-        fft<H, TC, true>(x, col, cx.stw_c, g, gm);
+        fft<H, TC, true>(x, col, cx.stw_c, g, gm, key);
 #pragma unroll
-        for (int e = 0; e < EC; ++e) col[P(g + TC * e)] = x[e];
+        for (int e = 0; e < EC; ++e) col[P(g + TC * e, key)] = x[e];
         __syncwarp(gm);
     }
 }
 
 // ------------------------------------------------------------------ row transforms
+// Swizzled position of row i in the spectrum columns a row lane g touches:
+// P(i, 4 cl) with cl = g + TR e - q MC, whose key mod 16 is 4 (g mod 4) for
+// every element (TR and MC are multiples of 4).
+template <class G>
+__device__ __forceinline__ int row_slot(int i, int g) {
+    static_assert(G::TR % 4 == 0 && G::MC % 4 == 0, "row-lane swizzle key");
+    return P(i, 4 * (g & 3));
+}
+
 // Pair every element of a row with its mirror column M-k (see the file
 // comment) and apply op(k, X[k], X[M-k]) in place.  Elements are taken in pairs
 // (e, ER-1-e), whose mirrors in lanes g >= 1 are each other's; lane 0's
@@ -320,15 +327,16 @@ __device__ __forceinline__ void row_inverse(const Ctx<G>& cx, typename G::V* rs,
                                             typename G::V (&x)[G::ER]) {
     using V = typename G::V;
     constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
+    const int pi = row_slot<G>(i, g);
 #pragma unroll
     for (int e = 0; e < ER; ++e) {
         const int k = g + TR * e;
         if constexpr (G::STATIC_OWNER) {
             const int q = (TR * e) / MC;  // compile-time after unrolling
-            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + P(i)];
+            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + pi];
         } else {
             const int q = k / MC;
-            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + P(i)];
+            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + pi];
         }
     }
     const V* tw = cx.tw;
@@ -362,15 +370,16 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
         const V w = tw[k * (NTW / W)];
         return cadd(E, cmul(w, O));
     });
+    const int pi = row_slot<G>(i, g);
 #pragma unroll
     for (int e = 0; e < ER; ++e) {
         const int k = g + TR * e;
         if constexpr (G::STATIC_OWNER) {
             const int q = (TR * e) / MC;
-            remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + P(i)] = z[e];
+            remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + pi] = z[e];
         } else {
             const int q = k / MC;
-            remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + P(i)] = z[e];
+            remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + pi] = z[e];
         }
     }
 }
