@@ -194,6 +194,27 @@ PCS_API pcs_status pcs_solve_slices_f64(const double *field, const unsigned char
                                         double lambda, double tau, double sigma, int n_iter, double *chi_out,
                                         int b0_axis, void *cuda_stream);
 
+/* ---------------------------------------------------------------- preprocessing */
+
+/*
+ * The preprocessing step of Sec. II.B (1): from the two acquisitions without
+ * (s0) and with (s1) the readout shift T_shift (Sec. II), the local field dB,
+ * the weighting W and the mask that Eq. (1) takes.
+ *   dB (ppm)  = arg(s1 conj s0) / (2 pi gamma_bar B0 T_shift) * 1e6, gamma_bar =
+ *               42.577478518 MHz/T; the wrapped phase in (-pi, pi], no unwrapping;
+ *               0 outside the mask
+ *   W         = |s0| / max |s0| over the n voxels
+ *   mask      = |s0|^2 >= threshold^2 max |s0|^2 (float32, reproducible bit for bit)
+ * s0, s1: device complex float32, interleaved (re, im), n_voxels each, 8-byte
+ * aligned.  field_out, weight_out: device float32 [n_voxels]; mask_out: device
+ * uint8 [n_voxels].  Asynchronous on cuda_stream (a 4-byte stream-ordered
+ * scratch allocation).  Errors: PCS_EINVAL (NULL, misaligned, t_shift or b0 <= 0,
+ * threshold < 0), PCS_ECUDA.  n_voxels = 0 is a no-op.
+ */
+PCS_API pcs_status pcs_field_map(const float *s0, const float *s1, size_t n_voxels, double t_shift_s,
+                                 double b0_tesla, double threshold, float *field_out, float *weight_out,
+                                 unsigned char *mask_out, void *cuda_stream);
+
 /* ---------------------------------------------------------------- 3-D variant */
 
 /*

@@ -152,6 +152,7 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_slices_weighted": (i, [vp, vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_volume_3d": (i, [vp, vp, i, i, i, d, d, d, i, i, vp, vp]),
         "pcs_supported_volume_3d": (i, [i, i, i]),
+        "pcs_field_map": (i, [vp, vp, ctypes.c_size_t, d, d, d, vp, vp, vp, vp]),
         "pcs_report": (i, [vp, vp, vp, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_monitored": (i, [vp, vp, vp, i, d, d, d, i, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
@@ -292,6 +293,25 @@ def pcs_solve_volume_3d(field, mask, lam: float, tau: float, sigma: float, n_ite
     st = (stream or torch.cuda.current_stream()).cuda_stream
     _check(load_library().pcs_solve_volume_3d(f, m, S, H, W, lam, tau, sigma, n_iter, tv, c, ctypes.c_void_p(st)),
            "pcs_solve_volume_3d")
+
+
+def pcs_field_map(s0, s1, t_shift_s: float, b0_tesla: float, threshold: float, field_out, weight_out, mask_out,
+                  stream=None):
+    """Field map (ppm), weighting and mask from two complex64 CUDA tensors of the same shape."""
+    import torch
+
+    shape = tuple(s0.shape)
+    a = _dev_ptr(torch.view_as_real(s0), "float32", shape + (2,), "s0")
+    b = _dev_ptr(torch.view_as_real(s1), "float32", shape + (2,), "s1")
+    f = _dev_ptr(field_out, "float32", shape, "field_out")
+    w = _dev_ptr(weight_out, "float32", shape, "weight_out")
+    m = _dev_ptr(mask_out, "uint8", shape, "mask_out")
+    n = 1
+    for x in shape:
+        n *= x
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(load_library().pcs_field_map(a, b, n, t_shift_s, b0_tesla, threshold, f, w, m, ctypes.c_void_p(st)),
+           "pcs_field_map")
 
 
 def pcs_supported_volume_3d(S: int, H: int, W: int) -> bool:

@@ -20,6 +20,7 @@ from .generator import (  # noqa: F401
     volume,
     config2,
     magnitude_weight,
+    echo_pair,
     config4_volumes,
     config5_arrivals,
 )

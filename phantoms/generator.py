@@ -242,6 +242,31 @@ def magnitude_weight(mask: np.ndarray, seed: int, floor: float = 0.2) -> np.ndar
     return np.ascontiguousarray(np.where(m, w, 0.0), dtype=np.float32)
 
 
+def echo_pair(field_ppm: np.ndarray, mask: np.ndarray, seed: int, b0_tesla: float = 3.0,
+              t_shift_s: float = 0.6e-3, noise: float = 0.002):
+    """Two complex acquisitions (without and with the readout shift) of a local field.
+
+    Forward model of the acquisition only: magnitude = a smooth image in
+    [0.2, 1] inside the mask and 0.02 outside (``magnitude_weight`` recipe),
+    a smooth receiver phase phi0 common to both, and the shifted one accrues
+    2 pi gamma_bar B0 T_shift dB (gamma_bar = 42.577478518 MHz/T, dB in ppm);
+    complex Gaussian noise of standard deviation ``noise`` on each.  Draws
+    from ``default_rng(seed)``.  Returns (s0, s1) complex64 [S][H][W].
+    """
+    rng = np.random.default_rng(seed)
+    mag = magnitude_weight(mask, seed + 1).astype(np.float64)
+    mag = np.where(np.asarray(mask) != 0, mag, 0.02)
+    phi0 = ndimage.gaussian_filter(rng.standard_normal(mag.shape), sigma=(1.0, 8.0, 8.0))
+    phi0 *= math.pi / max(float(np.abs(phi0).max()), 1e-30)
+    rad_per_ppm = 2.0 * math.pi * 42.577478518e6 * b0_tesla * t_shift_s * 1e-6
+    s0 = mag * np.exp(1j * phi0)
+    s1 = s0 * np.exp(1j * rad_per_ppm * np.asarray(field_ppm, dtype=np.float64))
+    shape = mag.shape
+    s0 = s0 + noise * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    s1 = s1 + noise * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    return s0.astype(np.complex64), s1.astype(np.complex64)
+
+
 def config2(S: int = 64) -> SliceProblem:
     """256x256x64 volume, six seeds/needles, lambda = 5e-4, 500 iterations, seed 0."""
     return volume(256, 256, S, seed=0, lam=5e-4, n_iter=500, name=f"cfg2-256x256x{S}")
