@@ -152,6 +152,30 @@ PCS_API pcs_status pcs_solve_slices_weighted(pcs_ctx *ctx, const float *field, c
                                              double sigma, int n_iter, float *chi_out, pcs_slice_report *rep);
 
 /*
+ * Balanced schedule.  When a solve has more slices than the kernel variant can
+ * keep resident as clusters (e.g. 64 slices of 256 x 256 on the 512-thread
+ * variant, 36 resident clusters), pcs_solve_slices spreads the S x n_iter
+ * slice-iterations evenly over the clusters (McNaughton's wrap-around rule):
+ * some slices are split in two consecutive parts run by two clusters, the
+ * second part continuing from the state the first left in memory (the same
+ * continuation as the monitored solves; results are unchanged, bit for bit).
+ * The second part waits for a flag the first sets; the wait is bounded
+ * (about 2 s) and never expected to run out.  If it does, the cluster returns
+ * early, the launch's results are invalid and pcs_check reports it.
+ *
+ * pcs_check: synchronise the context's stream and return PCS_ECUDA if any
+ * earlier solve on it gave up a wait (clearing the report), else PCS_OK.
+ */
+PCS_API pcs_status pcs_check(pcs_ctx *ctx);
+
+/*
+ * Test of the schedule's bounded wait: one warp waits on a flag that nothing
+ * sets, with a limit of limit_cycles SM clock cycles, and *gave_up (host) is
+ * set to 1 when the wait gave up.  Synchronises cuda_stream.
+ */
+PCS_API pcs_status pcs_selftest_wait(void *cuda_stream, long long limit_cycles, int *gave_up);
+
+/*
  * Same as pcs_solve_slices, but field, mask and chi_out are HOST buffers
  * (pinned memory gives full copy bandwidth).  Copies the inputs to
  * library-owned device staging buffers, solves, copies chi back and

@@ -153,6 +153,8 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_volume_3d": (i, [vp, vp, i, i, i, d, d, d, i, i, vp, vp]),
         "pcs_supported_volume_3d": (i, [i, i, i]),
         "pcs_field_map": (i, [vp, vp, ctypes.c_size_t, d, d, d, vp, vp, vp, vp]),
+        "pcs_check": (i, [vp]),
+        "pcs_selftest_wait": (i, [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
         "pcs_report": (i, [vp, vp, vp, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_monitored": (i, [vp, vp, vp, i, d, d, d, i, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_opnorm": (i, [vp, vp, i, i, ctypes.POINTER(d)]),
@@ -312,6 +314,21 @@ def pcs_field_map(s0, s1, t_shift_s: float, b0_tesla: float, threshold: float, f
     st = (stream or torch.cuda.current_stream()).cuda_stream
     _check(load_library().pcs_field_map(a, b, n, t_shift_s, b0_tesla, threshold, f, w, m, ctypes.c_void_p(st)),
            "pcs_field_map")
+
+
+def pcs_check(ctx):
+    """Synchronise the context's stream; raise if an earlier solve gave up a bounded wait."""
+    _check(load_library().pcs_check(ctx), "pcs_check")
+
+
+def pcs_selftest_wait(limit_cycles: int, stream=None) -> bool:
+    """Run the schedule's bounded wait on a flag nothing sets; True if it gave up."""
+    import torch
+
+    out = ctypes.c_int(0)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(load_library().pcs_selftest_wait(ctypes.c_void_p(st), limit_cycles, ctypes.byref(out)), "pcs_selftest_wait")
+    return bool(out.value)
 
 
 def pcs_supported_volume_3d(S: int, H: int, W: int) -> bool:

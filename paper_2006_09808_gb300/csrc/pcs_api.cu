@@ -157,6 +157,13 @@ struct pcs_ctx {
     float* xa = nullptr;
     float* xb = nullptr;
     int* active = nullptr;  // monitored solves: per-slice flags
+    // balanced schedule (more slices than resident clusters): segments, offsets, per-slice
+    // flags, and the key (S, n_iter, clusters) the uploaded schedule was built for
+    int4* sched = nullptr;
+    int* sched_off = nullptr;
+    int* seg_flags = nullptr;
+    int sched_S = -1, sched_N = -1, sched_K = -1;
+    int* err = nullptr;  // device error word of the schedule's bounded waits
     // CUDA-graph replay (use_graph): the last captured solve and its arguments
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -169,8 +176,9 @@ namespace {
 
 void free_ctx(pcs_ctx* c) {
     if (!c) return;
-    void* ptrs[] = {c->dtab,     c->ddtab,  c->twid,    c->chibar, c->p,   c->qx,  c->qy,
-                    c->st_field, c->st_mask, c->st_chi, c->partials, c->Ldev, c->xa, c->xb, c->active};
+    void* ptrs[] = {c->dtab,     c->ddtab,  c->twid,     c->chibar, c->p,  c->qx,   c->qy,
+                    c->st_field, c->st_mask, c->st_chi,  c->partials, c->Ldev, c->xa,  c->xb,
+                    c->active,   c->sched,   c->sched_off, c->seg_flags, c->err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -195,6 +203,36 @@ pcs_status validate_solve(pcs_ctx* ctx, const void* field, const void* mask, int
     if (field == chi_out) return fail(PCS_EINVAL, "chi_out must not alias field");
     return PCS_OK;
 }
+
+// McNaughton's wrap-around rule over clusters with the slices' iterations laid end to end:
+// cluster c covers positions [c T, (c+1) T), T = ceil(S N / K) >= N, so a slice is split at most
+// once.  Each cluster runs its pieces in reverse order, so the first part of a split slice (the
+// end of one cluster's range) runs at the start of that cluster's time and its second part (the
+// start of the next cluster's range) at the end of the next cluster's time: with equal speeds
+// the first part is done T - N iterations early, and the second waits on a flag only as a
+// guard.  Segment = (slice, first iteration, end iteration, bit 0 wait / bit 1 signal).
+void build_schedule(int S, int N, int K, std::vector<int4>& segs, std::vector<int>& off) {
+    segs.clear();
+    off.assign(K + 1, 0);
+    const long long U = (long long)S * N;
+    const long long T = (U + K - 1) / K;
+    for (int c = 0; c < K; ++c) {
+        off[c] = (int)segs.size();
+        const long long lo = c * T, hi = std::min(U, lo + T);
+        std::vector<int4> pieces;
+        for (long long q = lo; q < hi;) {
+            const int sl = (int)(q / N);
+            const int b = (int)(q - (long long)sl * N);
+            const int e = (int)std::min<long long>(N, b + (hi - q));
+            pieces.push_back(make_int4(sl, b, e, (b > 0 ? 1 : 0) | (e < N ? 2 : 0)));
+            q += e - b;
+        }
+        for (auto it = pieces.rbegin(); it != pieces.rend(); ++it) segs.push_back(*it);
+    }
+    off[K] = (int)segs.size();
+}
+
+constexpr long long kWaitLimitCycles = 4000000000LL;  // ~2 s at the maximum SM clock
 
 pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
                         double tau, double sigma, int n_iter, float* chi_out,
@@ -230,8 +268,45 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     if (ncl > S) ncl = S;
     if (ncl < 1) ncl = 1;
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    // more slices than resident clusters: balance the iterations over the clusters (streaming
+    // kernel, plain solves; the monitored path's active flags keep whole slices)
+    const bool balanced = !active && ncl < S && n_iter > 0 && (entry ? entry : ctx->entry)->launch_sched;
+    if (balanced) {
+        if (!ctx->sched) {
+            const size_t nseg = (size_t)ctx->max_slices * 2 + 1;
+            PCS_CUDA(cudaMalloc(&ctx->sched, nseg * sizeof(int4)), "cudaMalloc schedule");
+            PCS_CUDA(cudaMalloc(&ctx->sched_off, (size_t)(ctx->max_slices + 1) * sizeof(int)), "cudaMalloc schedule");
+            PCS_CUDA(cudaMalloc(&ctx->seg_flags, (size_t)ctx->max_slices * sizeof(int)), "cudaMalloc flags");
+        }
+        if (ctx->sched_S != S || ctx->sched_N != n_iter || ctx->sched_K != ncl) {
+            std::vector<int4> segs;
+            std::vector<int> off;
+            build_schedule(S, n_iter, ncl, segs, off);
+            PCS_CUDA(cudaMemcpyAsync(ctx->sched, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                     ctx->stream), "schedule upload");
+            PCS_CUDA(cudaMemcpyAsync(ctx->sched_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                     ctx->stream), "schedule upload");
+            PCS_CUDA(cudaStreamSynchronize(ctx->stream), "schedule upload");  // host vectors go out of scope
+            ctx->sched_S = S;
+            ctx->sched_N = n_iter;
+            ctx->sched_K = ncl;
+        }
+        prm.sched = ctx->sched;
+        prm.sched_off = ctx->sched_off;
+        prm.seg_flags = ctx->seg_flags;
+        prm.err = ctx->err;
+        prm.wait_limit = kWaitLimitCycles;
+    }
+    // the flags are cleared on the stream right before every launch (inside a captured graph too)
+    auto launch = [&](const pcs::KernelEntry* e) -> cudaError_t {
+        if (balanced) {
+            cudaError_t me = cudaMemsetAsync(ctx->seg_flags, 0, (size_t)S * sizeof(int), ctx->stream);
+            if (me != cudaSuccess) return me;
+        }
+        return balanced ? e->launch_sched(prm, ncl, ctx->stream) : e->launch(prm, ncl, ctx->stream);
+    };
     if (entry && entry != ctx->entry) {  // another variant of the same size (monitored solves)
-        PCS_CUDA(entry->launch(prm, ncl, ctx->stream), "launch of the primal-dual kernel");
+        PCS_CUDA(launch(entry), "launch of the primal-dual kernel");
         ctx->last_iters = n_iter;
         return PCS_OK;
     }
@@ -245,7 +320,7 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
             ctx->graph_exec = nullptr;
             ctx->graph = nullptr;
             PCS_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
-            cudaError_t le = ctx->entry->launch(prm, ncl, ctx->stream);
+            cudaError_t le = launch(ctx->entry);
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
             if (le != cudaSuccess) {
@@ -260,10 +335,15 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
         }
         PCS_CUDA(cudaGraphLaunch(ctx->graph_exec, ctx->stream), "graph launch");
     } else {
-        PCS_CUDA(ctx->entry->launch(prm, ncl, ctx->stream), "launch of the primal-dual kernel");
+        PCS_CUDA(launch(ctx->entry), "launch of the primal-dual kernel");
     }
     ctx->last_iters = n_iter;
     return PCS_OK;
+}
+
+// Bounded wait of the balanced schedule on a flag nothing sets.
+__global__ void wait_selftest_kernel(const int* flag, long long limit, int* out) {
+    if (threadIdx.x == 0) out[0] = pcs::wait_flag(flag, limit) ? 0 : 1;
 }
 
 }  // namespace
@@ -418,15 +498,46 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
         {(void**)&c->dtab, dtab.size() * sizeof(float)},  {(void**)&c->ddtab, ddtab.size() * sizeof(float)},
         {(void**)&c->twid, tw.size() * sizeof(float2)},   {(void**)&c->chibar, n * sizeof(float)},
         {(void**)&c->p, n * sizeof(float)},               {(void**)&c->qx, n * sizeof(float)},
-        {(void**)&c->qy, n * sizeof(float)},
+        {(void**)&c->qy, n * sizeof(float)},              {(void**)&c->err, sizeof(int)},
     };
     for (auto& a : allocs)
         if ((e = cudaMalloc(a.ptr, a.bytes)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
     if ((e = cudaMemcpy(c->dtab, dtab.data(), dtab.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(c->ddtab, ddtab.data(), ddtab.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(c->twid, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        (e = cudaMemcpy(c->twid, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(c->err, 0, sizeof(int))) != cudaSuccess)
         return bail(cuda_fail(e, "table upload"));
     *out = c;
+    return PCS_OK;
+}
+
+pcs_status pcs_check(pcs_ctx* ctx) {
+    if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
+    PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int flag = 0;
+    PCS_CUDA(cudaMemcpyAsync(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "D2H error word");
+    PCS_CUDA(cudaStreamSynchronize(ctx->stream), "stream sync");
+    if (flag) {
+        PCS_CUDA(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream), "clear error word");
+        return fail(PCS_ECUDA, "a solve on this context gave up waiting for another cluster (its results are invalid)");
+    }
+    return PCS_OK;
+}
+
+pcs_status pcs_selftest_wait(void* cuda_stream, long long limit_cycles, int* gave_up) {
+    if (!gave_up || limit_cycles < 0) return fail(PCS_EINVAL, "bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int* d = nullptr;
+    PCS_CUDA(cudaMalloc(&d, 2 * sizeof(int)), "cudaMalloc");
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d, 0, 2 * sizeof(int), st)) == cudaSuccess) {
+        wait_selftest_kernel<<<1, 32, 0, st>>>(d, limit_cycles, d + 1);
+        if ((e = cudaGetLastError()) == cudaSuccess &&
+            (e = cudaMemcpyAsync(gave_up, d + 1, sizeof(int), cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+    }
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
     return PCS_OK;
 }
 

@@ -72,7 +72,35 @@ struct PDParamsT {
     int tv_iso;                 // 0: componentwise clamp (anisotropic TV); 1: unit-disc projection (isotropic)
     const Real* weight;         // NULL: data weighting W = mask; else W [S][H][W] (values in [0, 1])
     Real* qz;                   // 3-D variant only: z component of q [S][H][W]
+    // Balanced schedule (streaming kernel, more slices than resident clusters): cluster c
+    // runs the iteration segments sched[sched_off[c] .. sched_off[c+1]) = (slice, first
+    // iteration, end iteration, flags); flags bit 0: wait for seg_flags[slice] (the first part
+    // of the slice runs on another cluster), bit 1: set seg_flags[slice] when done.
+    const int4* sched;          // NULL: persistent loop over whole slices
+    const int* sched_off;       // [clusters + 1]
+    int* seg_flags;             // [S], zeroed before each launch
+    int* err;                   // set to 1 when a wait gives up (that launch's result is invalid)
+    long long wait_limit;       // clock64 cycles a cluster waits before giving up
 };
+
+// Bounded wait for *flag != 0 (acquire, GPU scope).  Returns false once `limit`
+// clock64 cycles have passed without the flag being set.
+__device__ __forceinline__ bool wait_flag(const int* flag, long long limit) {
+    const long long t0 = clock64();
+    while (true) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v != 0) return true;
+        if (clock64() - t0 > limit) return false;
+        __nanosleep(200);
+    }
+}
+
+// Release a flag (GPU scope) after the writes that precede it.
+__device__ __forceinline__ void set_flag(int* flag) {
+    __threadfence();
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag), "r"(1) : "memory");
+}
 
 // Dual TV prox of one pixel: v = q + sigma M G chibar; clamp each component, or
 // project (vx, vy) onto the unit disc.
@@ -143,7 +171,9 @@ struct Geo {
     static constexpr int SM_TW = NTW;
     static constexpr int SM_STW_R = StageTw<M, ER>::SIZE;  // row-transform stage twiddles
     static constexpr int SM_STW_C = StageTw<H, EC>::SIZE;  // column-transform stage twiddles
-    static constexpr size_t SMEM_BYTES = sizeof(V) * (SM_TBUF + SM_ROWS + SM_TW + SM_STW_R + SM_STW_C);
+    // + 16 bytes: a cluster's decision word (balanced schedule).  No static shared memory in
+    // these kernels: it would shift the dynamic buffer off the alignment the swizzle relies on.
+    static constexpr size_t SMEM_BYTES = sizeof(V) * (SM_TBUF + SM_ROWS + SM_TW + SM_STW_R + SM_STW_C) + 16;
 
     static_assert(TR <= 32 && TC <= 32, "group fits a warp");
     static_assert(R % RPP == 0, "row passes");
@@ -609,59 +639,101 @@ __device__ __forceinline__ void rows_forward_state(const Ctx<G>& cx, const typen
 
 // ------------------------------------------------------------------ kernel
 
+// Iterations [it_b, it_e) of slice s: a zero start when it_b = 0 (and no resume),
+// else a continuation from the stored state.
 template <class G>
-__global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParamsT<typename G::Real> prm) {
+__device__ __forceinline__ void run_slice(Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, int s, int it_b,
+                                          int it_e) {
     using V = typename G::V;
     using Real = typename G::Real;
+    constexpr size_t SLICE = (size_t)G::H * G::W;
+    constexpr int OWN = G::R * G::W;  // floats of own rows
+    const size_t base = (size_t)s * SLICE;
+    const Real inv_den = slice_inv_den(prm, s);
+    const bool cont = prm.resume || it_b > 0;
+    if (cont) {
+        // continue: the spectrum of the stored chibar, then the loop as after iteration 0
+        cluster_barrier<G::C>();  // peers running before their shared memory is written
+        rows_forward_state<G>(cx, prm.chibar, base);
+    } else {
+        // zero start (pseudocode steps 2-3): chi, chibar, p, q of own rows, own spectrum
+        const size_t o = base + (size_t)cx.crank * OWN;
+        V* ptrs[5] = {reinterpret_cast<V*>(prm.chi + o), reinterpret_cast<V*>(prm.chibar + o),
+                      reinterpret_cast<V*>(prm.p + o), reinterpret_cast<V*>(prm.qx + o),
+                      reinterpret_cast<V*>(prm.qy + o)};
+        const V z2 = mk<V>(Real(0), Real(0));
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+            for (int t = threadIdx.x; t < OWN / 2; t += G::NT) __stcg(ptrs[a] + t, z2);
+        for (int t = threadIdx.x; t < G::SM_TBUF; t += G::NT) cx.tbuf[t] = mk<V>(Real(0), Real(0));
+    }
+    // half-steps: even = column pass (u-spectrum = D F chibar_n; skipped at a zero
+    // start, where it is zero) + dual phase, odd = column pass (v-spectrum = D F W p_{n+1})
+    // + primal phase.  Each phase appears once in the code.  A row phase is
+    // entered after cluster_arrive() and waits inside, after its own-row loads.
+    const int nh = 2 * (it_e - it_b);
+#pragma unroll 1
+    for (int h = 0; h < nh; ++h) {
+        if (h > 0 || cont) {
+            cluster_barrier<G::C>();
+            column_pass<G>(cx, prm.dtab, prm.ddtab);
+        }
+        cluster_arrive<G::C>();
+        if ((h & 1) == 0) {
+            phase_dual<G>(cx, prm, base, inv_den, h > 0 || cont);
+        } else {
+            phase_primal<G>(cx, prm, base, h + 1 == nh);
+        }
+    }
+    cluster_barrier<G::C>();  // the last phase's gathers done before the next slice writes
+}
+
+// SCHED: run the balanced schedule's segments (a separate instantiation: the plain
+// persistent loop keeps the registers the schedule's bookkeeping would take).
+template <class G, bool SCHED = false>
+__global__ void __launch_bounds__(G::NT, G::MINB) pd_cluster_kernel(PDParamsT<typename G::Real> prm) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Ctx<G> cx;
     ctx_init<G>(cx, smem_raw, prm.twid);
-
     const int cid = blockIdx.x / G::C;
-    const int ncl = gridDim.x / G::C;
-    constexpr size_t SLICE = (size_t)G::H * G::W;
-    constexpr int OWN = G::R * G::W;  // floats of own rows
-
+    if constexpr (!SCHED) {
 #pragma unroll 1
-    for (int s = cid; s < prm.S; s += ncl) {
-        if (prm.active && __ldg(prm.active + s) == 0) continue;  // same decision in every CTA of the cluster
-        const size_t base = (size_t)s * SLICE;
-        const Real inv_den = slice_inv_den(prm, s);
-        if (prm.resume) {
-            // continue: the spectrum of the stored chibar, then the loop as after iteration 0
-            cluster_barrier<G::C>();  // peers running before their shared memory is written
-            rows_forward_state<G>(cx, prm.chibar, base);
-        } else {
-            // zero start (pseudocode steps 2-3): chi, chibar, p, q of own rows, own spectrum
-            const size_t o = base + (size_t)cx.crank * OWN;
-            V* ptrs[5] = {reinterpret_cast<V*>(prm.chi + o), reinterpret_cast<V*>(prm.chibar + o),
-                          reinterpret_cast<V*>(prm.p + o), reinterpret_cast<V*>(prm.qx + o),
-                          reinterpret_cast<V*>(prm.qy + o)};
-            const V z2 = mk<V>(Real(0), Real(0));
-#pragma unroll
-            for (int a = 0; a < 5; ++a)
-                for (int t = threadIdx.x; t < OWN / 2; t += G::NT) __stcg(ptrs[a] + t, z2);
-            for (int t = threadIdx.x; t < G::SM_TBUF; t += G::NT) cx.tbuf[t] = mk<V>(Real(0), Real(0));
+        for (int s = cid; s < prm.S; s += gridDim.x / G::C) {
+            if (prm.active && __ldg(prm.active + s) == 0) continue;  // same decision in every CTA of the cluster
+            run_slice<G>(cx, prm, s, 0, prm.n_iter);
         }
-        // half-steps: even = column pass (u-spectrum = D F chibar_n; skipped at a zero
-        // start, where it is zero) + dual phase, odd = column pass (v-spectrum = D F W p_{n+1})
-        // + primal phase.  Each phase appears once in the code.  A row phase is
-        // entered after cluster_arrive() and waits inside, after its own-row loads.
-        const int nh = 2 * prm.n_iter;
+    } else {
 #pragma unroll 1
-        for (int h = 0; h < nh; ++h) {
-            if (h > 0 || prm.resume) {
+        for (int k = __ldg(prm.sched_off + cid); k < __ldg(prm.sched_off + cid + 1); ++k) {
+            const int4 sg = __ldg(prm.sched + k);
+            if (sg.w & 1) {
+                // the slice's first part runs on another cluster: CTA 0 waits (bounded) and the
+                // cluster follows its decision (a word after the tables), so that every CTA
+                // proceeds or every CTA returns
+                int* go = reinterpret_cast<int*>(cx.stw_c + G::SM_STW_C);
+                if (cx.crank == 0 && threadIdx.x == 0)
+                    *go = wait_flag(prm.seg_flags + sg.x, prm.wait_limit) ? 1 : 0;
                 cluster_barrier<G::C>();
-                column_pass<G>(cx, prm.dtab, prm.ddtab);
+                int ok;
+                if constexpr (G::C == 1) {
+                    ok = *go;
+                } else {
+                    ok = *cg::this_cluster().map_shared_rank(go, 0);
+                }
+                cluster_barrier<G::C>();  // every CTA has read CTA 0's decision
+                if (!ok) {
+                    if (cx.crank == 0 && threadIdx.x == 0) atomicExch(prm.err, 1);
+                    return;
+                }
+                if (threadIdx.x == 0) (void)wait_flag(prm.seg_flags + sg.x, prm.wait_limit);  // this CTA's acquire
+                __syncthreads();
             }
-            cluster_arrive<G::C>();
-            if ((h & 1) == 0) {
-                phase_dual<G>(cx, prm, base, inv_den, h > 0 || prm.resume);
-            } else {
-                phase_primal<G>(cx, prm, base, h + 1 == nh);
+            run_slice<G>(cx, prm, sg.x, sg.y, sg.z);
+            if (cx.crank == 0 && threadIdx.x == 0) {
+                const int4 done = __ldg(prm.sched + k);
+                if (done.w & 2) set_flag(prm.seg_flags + done.x);
             }
         }
-        cluster_barrier<G::C>();  // the last phase's gathers done before the next slice writes
     }
 }
 

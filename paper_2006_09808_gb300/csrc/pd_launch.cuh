@@ -22,6 +22,8 @@ struct KernelEntry {
     cudaError_t (*launch)(const PDParams& prm, int n_clusters, cudaStream_t stream);
     cudaError_t (*launch_report)(const AuxParams& prm, int n_clusters, cudaStream_t stream);
     cudaError_t (*launch_opnorm)(const AuxParams& prm, int n_clusters, cudaStream_t stream);
+    // the balanced-schedule instantiation of the iteration kernel (NULL for the resident kernel)
+    cudaError_t (*launch_sched)(const PDParams& prm, int n_clusters, cudaStream_t stream);
 };
 
 template <class G>
@@ -73,6 +75,10 @@ cudaError_t launch_pd(const PDParams& prm, int n_clusters, cudaStream_t stream) 
     return launch_cluster<G>(pd_cluster_kernel<G>, prm, G::SMEM_BYTES, n_clusters, stream);
 }
 template <class G>
+cudaError_t launch_pd_sched(const PDParams& prm, int n_clusters, cudaStream_t stream) {
+    return launch_cluster<G>(pd_cluster_kernel<G, true>, prm, G::SMEM_BYTES, n_clusters, stream);
+}
+template <class G>
 cudaError_t launch_report(const AuxParams& prm, int n_clusters, cudaStream_t stream) {
     return launch_cluster<G>(aux_report_kernel<G>, prm, aux_smem<G>(), n_clusters, stream);
 }
@@ -85,7 +91,9 @@ template <class G>
 cudaError_t prepare_all(int* max_clusters, int* max_clusters_aux) {
     cudaError_t e = prepare_cluster<G>(pd_cluster_kernel<G>, G::SMEM_BYTES, max_clusters);
     if (e != cudaSuccess) return e;
-    int a = 0, b = 0;
+    int a = 0, b = 0, c = 0;
+    if ((e = prepare_cluster<G>(pd_cluster_kernel<G, true>, G::SMEM_BYTES, &c)) != cudaSuccess) return e;
+    if (c < *max_clusters) *max_clusters = c;
     if ((e = prepare_cluster<G>(aux_report_kernel<G>, aux_smem<G>(), &a)) != cudaSuccess) return e;
     if ((e = prepare_cluster<G>(aux_opnorm_kernel<G>, aux_smem<G>(), &b)) != cudaSuccess) return e;
     *max_clusters_aux = a < b ? a : b;
@@ -96,7 +104,7 @@ template <class G>
 constexpr KernelEntry make_entry() {
     return KernelEntry{G::H,           G::W,           G::C,       0,
                        G::SMEM_BYTES,  G::NT,          &prepare_all<G>,
-                       &launch_pd<G>,  &launch_report<G>, &launch_opnorm<G>};
+                       &launch_pd<G>,  &launch_report<G>, &launch_opnorm<G>, &launch_pd_sched<G>};
 }
 
 // Resident variant: the iteration kernel keeps the state on chip; the
@@ -121,7 +129,7 @@ constexpr KernelEntry make_resident_entry() {
     using G = typename GR::B;
     return KernelEntry{GR::H,           GR::W,          GR::C,       1,
                        GR::SMEM_BYTES,  GR::NT,         &prepare_res<GR>,
-                       &launch_res<GR>, &launch_report<G>, &launch_opnorm<G>};
+                       &launch_res<GR>, &launch_report<G>, &launch_opnorm<G>, nullptr};
 }
 
 // FP64 variant (precision study): iteration kernel only.
