@@ -169,6 +169,17 @@ PCS_API pcs_status pcs_solve_slices_weighted(pcs_ctx *ctx, const float *field, c
 PCS_API pcs_status pcs_check(pcs_ctx *ctx);
 
 /*
+ * The balanced schedule a solve of S slices x n_iter iterations uses on
+ * `clusters` resident clusters (1 <= clusters < S): segments[4k .. 4k+3] =
+ * (slice, first iteration, end iteration, flags: 1 = waits for the slice's
+ * first part, 2 = releases its continuation), cluster c running segments
+ * [offsets[c], offsets[c+1]) in that order.  *n_segments: capacity in, count
+ * out; with segments or offsets NULL only the count is returned.  Host only.
+ */
+PCS_API pcs_status pcs_schedule_plan(int S, int n_iter, int clusters, int *segments, int *n_segments,
+                                     int *offsets);
+
+/*
  * Test of the schedule's bounded wait: one warp waits on a flag that nothing
  * sets, with a limit of limit_cycles SM clock cycles, and *gave_up (host) is
  * set to 1 when the wait gave up.  Synchronises cuda_stream.

@@ -154,6 +154,8 @@ def load_library(path: str = LIB_PATH):
         "pcs_supported_volume_3d": (i, [i, i, i]),
         "pcs_field_map": (i, [vp, vp, ctypes.c_size_t, d, d, d, vp, vp, vp, vp]),
         "pcs_check": (i, [vp]),
+        "pcs_schedule_plan": (i, [i, i, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]),
         "pcs_selftest_wait": (i, [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]),
         "pcs_report": (i, [vp, vp, vp, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_monitored": (i, [vp, vp, vp, i, d, d, d, i, i, d, vp, ctypes.POINTER(pcs_slice_report)]),
@@ -314,6 +316,17 @@ def pcs_field_map(s0, s1, t_shift_s: float, b0_tesla: float, threshold: float, f
     st = (stream or torch.cuda.current_stream()).cuda_stream
     _check(load_library().pcs_field_map(a, b, n, t_shift_s, b0_tesla, threshold, f, w, m, ctypes.c_void_p(st)),
            "pcs_field_map")
+
+
+def pcs_schedule_plan(S: int, n_iter: int, clusters: int):
+    """The balanced schedule: ([(slice, first, end, flags), ...], offsets per cluster)."""
+    lib = load_library()
+    n = ctypes.c_int(0)
+    _check(lib.pcs_schedule_plan(S, n_iter, clusters, None, ctypes.byref(n), None), "pcs_schedule_plan")
+    segs = (ctypes.c_int * (4 * n.value))()
+    off = (ctypes.c_int * (clusters + 1))()
+    _check(lib.pcs_schedule_plan(S, n_iter, clusters, segs, ctypes.byref(n), off), "pcs_schedule_plan")
+    return [tuple(segs[4 * k:4 * k + 4]) for k in range(n.value)], list(off)
 
 
 def pcs_check(ctx):

@@ -511,6 +511,26 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
     return PCS_OK;
 }
 
+pcs_status pcs_schedule_plan(int S, int n_iter, int clusters, int* segments, int* n_segments, int* offsets) {
+    if (S < 1 || n_iter < 1 || clusters < 1 || clusters >= S || !n_segments)
+        return fail(PCS_EINVAL, "needs 1 <= clusters < S and n_iter >= 1");
+    std::vector<int4> segs;
+    std::vector<int> off;
+    build_schedule(S, n_iter, clusters, segs, off);
+    const int cap = *n_segments;
+    *n_segments = (int)segs.size();
+    if (!segments || !offsets) return PCS_OK;  // size query
+    if (cap < (int)segs.size()) return fail(PCS_EINVAL, "segments holds %d entries, %zu needed", cap, segs.size());
+    for (size_t k = 0; k < segs.size(); ++k) {
+        segments[4 * k + 0] = segs[k].x;
+        segments[4 * k + 1] = segs[k].y;
+        segments[4 * k + 2] = segs[k].z;
+        segments[4 * k + 3] = segs[k].w;
+    }
+    for (int c = 0; c <= clusters; ++c) offsets[c] = off[c];
+    return PCS_OK;
+}
+
 pcs_status pcs_check(pcs_ctx* ctx) {
     if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
