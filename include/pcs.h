@@ -258,7 +258,9 @@ PCS_API pcs_status pcs_field_map(const float *s0, const float *s1, size_t n_voxe
  * reads G as 2-D and solves slices independently).  The volume [S][H][W] is
  * one unknown: D(k) = 1/3 - kz^2/|k|^2 with B0 along z (the slice axis),
  * periodic on the S x H x W grid, isotropic voxels; G = forward differences
- * along x, y, z with a Neumann boundary; W = M = mask.  The Sec. II.A
+ * along x, y, z with a Neumann boundary; M = mask, and W = mask when weight
+ * is NULL, else weight (device float32 [S][H][W], 16-byte aligned, values in
+ * [0, 1], as pcs_solve_slices_weighted).  The Sec. II.A
  * iteration runs n_iter times from the zero start (tau, sigma as for
  * pcs_solve_slices; ||K|| <= sqrt(4/9 + 12) for any 0/1 mask, so
  * tau = sigma = 1/3.53 is always valid).  tv: 0 anisotropic (clamp of each of
@@ -270,8 +272,8 @@ PCS_API pcs_status pcs_field_map(const float *s0, const float *s1, size_t n_voxe
  * H >= 128); others PCS_EUNSUPPORTED.  Errors: PCS_EINVAL for bad arguments,
  * PCS_ECUDA for CUDA failures.
  */
-PCS_API pcs_status pcs_solve_volume_3d(const float *field, const unsigned char *mask, int S, int H, int W,
-                                       double lambda, double tau, double sigma, int n_iter, int tv,
+PCS_API pcs_status pcs_solve_volume_3d(const float *field, const unsigned char *mask, const float *weight, int S,
+                                       int H, int W, double lambda, double tau, double sigma, int n_iter, int tv,
                                        float *chi_out, void *cuda_stream);
 
 /* 1 if pcs_solve_volume_3d has kernels for an S x H x W volume, else 0. */

@@ -150,7 +150,7 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_slices": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_host": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_weighted": (i, [vp, vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
-        "pcs_solve_volume_3d": (i, [vp, vp, i, i, i, d, d, d, i, i, vp, vp]),
+        "pcs_solve_volume_3d": (i, [vp, vp, vp, i, i, i, d, d, d, i, i, vp, vp]),
         "pcs_supported_volume_3d": (i, [i, i, i]),
         "pcs_field_map": (i, [vp, vp, ctypes.c_size_t, d, d, d, vp, vp, vp, vp]),
         "pcs_check": (i, [vp]),
@@ -286,16 +286,18 @@ def pcs_solve_slices_weighted(ctx, field, mask, weight, lam: float, tau: float, 
 
 
 def pcs_solve_volume_3d(field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, tv: int = 0,
-                        stream=None):
-    """3-D solve of one volume (field/mask/chi_out: [S][H][W] float32/uint8/float32 CUDA tensors)."""
+                        weight=None, stream=None):
+    """3-D solve of one volume (field/mask/chi_out: [S][H][W] float32/uint8/float32 CUDA tensors;
+    weight: optional float32 data weighting W, default W = mask)."""
     import torch
 
     S, H, W = field.shape
     f = _dev_ptr(field, "float32", (S, H, W), "field")
     m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    w = None if weight is None else _dev_ptr(weight, "float32", (S, H, W), "weight")
     c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
     st = (stream or torch.cuda.current_stream()).cuda_stream
-    _check(load_library().pcs_solve_volume_3d(f, m, S, H, W, lam, tau, sigma, n_iter, tv, c, ctypes.c_void_p(st)),
+    _check(load_library().pcs_solve_volume_3d(f, m, w, S, H, W, lam, tau, sigma, n_iter, tv, c, ctypes.c_void_p(st)),
            "pcs_solve_volume_3d")
 
 

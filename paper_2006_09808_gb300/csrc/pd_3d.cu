@@ -90,9 +90,11 @@ int pcs_supported_volume_3d(int S, int H, int W) {
     return (slice && z) ? 1 : 0;
 }
 
-pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, int S, int H, int W, double lambda,
-                               double tau, double sigma, int n_iter, int tv, float* chi_out, void* cuda_stream) {
+pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, const float* weight, int S, int H,
+                               int W, double lambda, double tau, double sigma, int n_iter, int tv, float* chi_out,
+                               void* cuda_stream) {
     if (!field || !mask || !chi_out) return fail3(PCS_EINVAL, "NULL argument");
+    if (!aligned16(weight)) return fail3(PCS_EINVAL, "weight must be 16-byte aligned");
     if (!(lambda > 0.0) || !(tau > 0.0) || !(sigma > 0.0)) return fail3(PCS_EINVAL, "lambda, tau, sigma must be > 0");
     if (n_iter < 0) return fail3(PCS_EINVAL, "n_iter must be >= 0");
     if (tv != 0 && tv != 1) return fail3(PCS_EINVAL, "tv must be 0 or 1");
@@ -147,6 +149,7 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, in
         a.pd.tau = (float)tau;
         a.pd.inv_den = (float)(1.0 / (1.0 + sigma / lambda));
         a.pd.tv_iso = tv;
+        a.pd.weight = weight;
         a.spec = spec;
         if (ncl > S) ncl = S;
         if (ncl < 1) ncl = 1;
