@@ -240,10 +240,10 @@ PCS_API pcs_status pcs_solve_slices_f64(const double *field, const unsigned char
  *               0 outside the mask
  *   W         = |s0| / max |s0| over the n voxels
  *   mask      = |s0|^2 >= threshold^2 max |s0|^2 (float32, reproducible bit for bit)
- * s0, s1: device complex float32, interleaved (re, im), n_voxels each, 8-byte
- * aligned.  field_out, weight_out: device float32 [n_voxels]; mask_out: device
- * uint8 [n_voxels].  Asynchronous on cuda_stream (a 4-byte stream-ordered
- * scratch allocation).  Errors: PCS_EINVAL (NULL, misaligned, t_shift or b0 <= 0,
+ * s0, s1: device complex float32, interleaved (re, im), n_voxels each, 16-byte
+ * aligned.  field_out, weight_out: device float32 [n_voxels], 8-byte aligned;
+ * mask_out: device uint8 [n_voxels], 2-byte aligned.  Asynchronous on
+ * cuda_stream (a small stream-ordered scratch allocation).  Errors: PCS_EINVAL (NULL, misaligned, t_shift or b0 <= 0,
  * threshold < 0), PCS_ECUDA.  n_voxels = 0 is a no-op.
  */
 PCS_API pcs_status pcs_field_map(const float *s0, const float *s1, size_t n_voxels, double t_shift_s,

@@ -107,3 +107,17 @@ def test_field_map_edges_and_errors():
     pcs.pcs_field_map(a, a, T_SHIFT, B0, 0.5, *out)
     torch.cuda.synchronize()
     assert torch.all(out[2] == 1) and torch.all(out[0] == 0) and torch.all(out[1] == 1)
+    # an odd voxel count (the last voxel is handled apart from the 16-byte pairs)
+    rng = np.random.default_rng(5)
+    shape = (3, 5, 7)
+    s0 = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+    s1 = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+    f, w, m = gpu_map(s0, s1, 0.4)
+    rf, rw, rm = FM.field_map(s0, s1, T_SHIFT, B0, 0.4)
+    assert np.array_equal(m, rm) and np.max(np.abs(w - rw)) <= 1e-6 and np.max(phase_err(f, rf)) <= 1e-5
+    # inputs off their 16-byte alignment are refused
+    z1 = torch.ones(17, dtype=torch.complex64, device="cuda")[1:]
+    o1 = [torch.empty(16, device="cuda"), torch.empty(16, device="cuda"), torch.empty(16, dtype=torch.uint8, device="cuda")]
+    with pytest.raises(pcs.PcsError) as ei:
+        pcs.pcs_field_map(z1, z1, T_SHIFT, B0, 0.1, *o1)
+    assert ei.value.status == pcs.PCS_EINVAL
