@@ -34,9 +34,10 @@
 // State (chi = the caller's chi_out, chibar, p, qx, qy) stays in global
 // memory (L2/HBM) and is touched once per phase; the FFT intermediates never
 // leave the chip.  The kernel is persistent: a cluster loops over slices
-// s = cluster_id, cluster_id + n_clusters, ...  There is no grid-wide
-// synchronisation and no spin-wait: the only waits are hardware cluster
-// barriers.
+// s = cluster_id, cluster_id + n_clusters, ..., or, with more slices than
+// clusters, over the segments of the balanced schedule (pd_cluster_kernel).
+// There is no grid-wide synchronisation; apart from hardware cluster barriers
+// the only wait is the schedule's bounded wait for a slice's first part.
 #pragma once
 
 #include <cooperative_groups.h>
