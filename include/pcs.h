@@ -268,13 +268,17 @@ PCS_API pcs_status pcs_field_map(const float *s0, const float *s1, size_t n_voxe
  * field, chi_out: device float32 [S][H][W]; mask: device uint8; 16-byte
  * aligned; chi_out must not alias field.  Allocates its scratch (6 floats and
  * a half spectrum per voxel), frees it and synchronises cuda_stream before
- * returning.  Shapes: H = W in {64, 128, 256}, S in {32, 64} (and 128 for
- * H >= 128); others PCS_EUNSUPPORTED.  Errors: PCS_EINVAL for bad arguments,
- * PCS_ECUDA for CUDA failures.
+ * returning.  rep (host, optional): the FP64 diagnostics of the whole volume
+ * at (chi_N, p_N, q_N), the terms of pcs_slice_report with D, G, W, M of this
+ * 3-D problem (the objective and the gap summed over all voxels; iters =
+ * n_iter); three more slice launches and two z passes, after the solve.
+ * Shapes: H = W in {64, 128, 256}, S in {32, 64} (and 128 for H >= 128);
+ * others PCS_EUNSUPPORTED.  Errors: PCS_EINVAL for bad arguments, PCS_ECUDA
+ * for CUDA failures.
  */
 PCS_API pcs_status pcs_solve_volume_3d(const float *field, const unsigned char *mask, const float *weight, int S,
                                        int H, int W, double lambda, double tau, double sigma, int n_iter, int tv,
-                                       float *chi_out, void *cuda_stream);
+                                       float *chi_out, pcs_slice_report *rep, void *cuda_stream);
 
 /* 1 if pcs_solve_volume_3d has kernels for an S x H x W volume, else 0. */
 PCS_API int pcs_supported_volume_3d(int S, int H, int W);

@@ -2,6 +2,7 @@
 // (pcs_solve_volume_3d; kernels in pd_3d.cuh).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -20,12 +21,15 @@ namespace {
 using pcs::Geo;
 using pcs::GeoZ;
 using pcs::P3Params;
+using pcs::P3Report;
 
 struct Slice3Entry {
-    int H, W;
+    int H, W, C;
     size_t smem;
     cudaError_t (*prepare)(int* max_clusters);
     cudaError_t (*launch)(const P3Params& a, int n_clusters, cudaStream_t st);
+    cudaError_t (*prepare_report)(int* max_clusters);
+    cudaError_t (*launch_report)(const P3Report& r, int n_clusters, cudaStream_t st);
 };
 
 template <class G>
@@ -37,8 +41,17 @@ cudaError_t launch3(const P3Params& a, int ncl, cudaStream_t st) {
     return pcs::launch_cluster<G>(pcs::pd3_slice_kernel<G>, a, G::SMEM_BYTES, ncl, st);
 }
 template <class G>
+cudaError_t prepare3_report(int* mc) {
+    return pcs::prepare_cluster<G>(pcs::pd3_report_kernel<G>, pcs::aux_smem<G>(), mc);
+}
+template <class G>
+cudaError_t launch3_report(const P3Report& r, int ncl, cudaStream_t st) {
+    return pcs::launch_cluster<G>(pcs::pd3_report_kernel<G>, r, pcs::aux_smem<G>(), ncl, st);
+}
+template <class G>
 constexpr Slice3Entry slice3_entry() {
-    return Slice3Entry{G::H, G::W, G::SMEM_BYTES, &prepare3<G>, &launch3<G>};
+    return Slice3Entry{G::H, G::W, G::C, G::SMEM_BYTES, &prepare3<G>, &launch3<G>, &prepare3_report<G>,
+                       &launch3_report<G>};
 }
 
 const Slice3Entry k_slice3[] = {
@@ -92,7 +105,7 @@ int pcs_supported_volume_3d(int S, int H, int W) {
 
 pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, const float* weight, int S, int H,
                                int W, double lambda, double tau, double sigma, int n_iter, int tv, float* chi_out,
-                               void* cuda_stream) {
+                               pcs_slice_report* rep, void* cuda_stream) {
     if (!field || !mask || !chi_out) return fail3(PCS_EINVAL, "NULL argument");
     if (!aligned16(weight)) return fail3(PCS_EINVAL, "weight must be 16-byte aligned");
     if (!(lambda > 0.0) || !(tau > 0.0) || !(sigma > 0.0)) return fail3(PCS_EINVAL, "lambda, tau, sigma must be > 0");
@@ -118,12 +131,15 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
     float* state = nullptr;  // chibar, p, qx, qy, qz
     float2* spec = nullptr;
     float2* twid = nullptr;
+    double* partial = nullptr;  // [S][C][kReportSums] when rep is set
+    const size_t npart = (size_t)S * se->C * pcs::kReportSums;
     cudaError_t e;
     int ncl = 0;
     pcs_status ret = PCS_OK;
     if ((e = cudaMalloc(&state, 5 * n * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&spec, nspec * sizeof(float2))) != cudaSuccess ||
-        (e = cudaMalloc(&twid, tw.size() * sizeof(float2))) != cudaSuccess) {
+        (e = cudaMalloc(&twid, tw.size() * sizeof(float2))) != cudaSuccess ||
+        (rep && (e = cudaMalloc(&partial, npart * sizeof(double))) != cudaSuccess)) {
         ret = fail3(PCS_ECUDA, "cudaMalloc", e);
     } else if ((e = cudaMemcpyAsync(twid, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st)) !=
                    cudaSuccess ||
@@ -172,13 +188,52 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
                 break;
             }
         }
+        // FP64 diagnostics at the final (chi, p, q): spectrum of chi, z pass, data and
+        // TV terms + spectrum of W p, z pass, stationarity
+        int ncl_rep = 0;
+        if (ret == PCS_OK && rep) {
+            if ((e = se->prepare_report(&ncl_rep)) != cudaSuccess) {
+                ret = fail3(PCS_ECUDA, "report set-up", e);
+            } else {
+                if (ncl_rep > S) ncl_rep = S;
+                if (ncl_rep < 1) ncl_rep = 1;
+                P3Report r;
+                std::memset(&r, 0, sizeof(r));
+                r.a = a;
+                r.partial = partial;
+                r.lam = lambda;
+                for (int mode = 0; mode < 3 && ret == PCS_OK; ++mode) {
+                    r.mode = mode;
+                    if ((e = se->launch_report(r, ncl_rep, st)) != cudaSuccess ||
+                        (mode < 2 && (e = ze->launch(spec, twid, ntw, st)) != cudaSuccess))
+                        ret = fail3(PCS_ECUDA, "report launch", e);
+                }
+            }
+        }
     }
     // synchronous: the call owns its scratch
     cudaError_t se2 = cudaStreamSynchronize(st);
     if (ret == PCS_OK && se2 != cudaSuccess) ret = fail3(PCS_ECUDA, "stream sync", se2);
+    if (ret == PCS_OK && rep) {
+        std::vector<double> h(npart);
+        if ((e = cudaMemcpy(h.data(), partial, npart * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            ret = fail3(PCS_ECUDA, "report copy", e);
+        } else {
+            // fixed-order sums: slice by slice, CTA by CTA
+            double t[pcs::kReportSums] = {0, 0, 0, 0, 0};
+            for (size_t k = 0; k < npart; ++k) t[k % pcs::kReportSums] += h[k];
+            rep->objective = 0.5 * lambda * t[0] + t[1];
+            rep->gap = t[2] / (2.0 * lambda) + t[3];
+            rep->stationarity = std::sqrt(t[4]);
+            rep->data_residual = std::sqrt(t[0]);
+            rep->iters = n_iter;
+            rep->pad = 0;
+        }
+    }
     cudaFree(state);
     cudaFree(spec);
     cudaFree(twid);
+    cudaFree(partial);
     return ret;
 }
 

@@ -21,6 +21,7 @@
 // multiplies every entry by a real D.
 #pragma once
 
+#include "pd_aux.cuh"
 #include "pd_cluster.cuh"
 
 namespace pcs {
@@ -136,6 +137,141 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd3_slice_kernel(P3Params a) {
         }
         cluster_barrier<G::C>();  // all scatters in; all gathers done
         if (a.store) columns_out_3d<G>(cx, a.spec, s);
+    }
+}
+
+// ------------------------------------------------------------------ FP64 diagnostics
+// At (chi, p, q) after the last iteration, per slice (sums over the slice's voxels;
+// the volume's values are their sums, the norms their root sums of squares):
+//   data_sq = ||W (D3 chi - dB)||^2, tv = ||M G3 chi||_1 (or the isotropic sum),
+//   fy1 = ||p - lambda W (D3 chi - dB)||^2, fy2 = sum(|g| - q.g) with g = M G3 chi,
+//   stat_sq = ||D3 W p + G3^T M q||^2.
+// Three launches of this kernel with z passes between them:
+//   mode 0: forward row and column transforms of chi -> spectrum
+//   mode 1: inverse transforms -> D3 chi: data and TV terms; forward transforms of W p -> spectrum
+//   mode 2: inverse transforms -> D3 W p: stationarity
+struct P3Report {
+    P3Params a;       // state, inputs, tables, spectrum
+    double* partial;  // [S][C][kReportSums]
+    double lam;
+    int mode;
+};
+
+template <class G>
+__global__ void __launch_bounds__(G::NT, 1) pd3_report_kernel(P3Report r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Ctx<G> cx;
+    ctx_init<G>(cx, smem_raw, r.a.pd.twid);
+    double* red = reinterpret_cast<double*>(cx.stw_c + G::SM_STW_C);
+    __syncthreads();
+    const PDParams& prm = r.a.pd;
+    constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
+    constexpr size_t SL = (size_t)H * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane % TR;
+    const int grp = warp * (32 / TR) + lane / TR;
+    const unsigned gm = group_mask<TR>(lane);
+    float2* rs = cx.rows + grp * G::MP;
+    const int cid = blockIdx.x / G::C, ncl = gridDim.x / G::C;
+    const double lam = r.lam;
+#pragma unroll 1
+    for (int s = cid; s < prm.S; s += ncl) {
+        const size_t base = (size_t)s * SL;
+        double acc[kReportSums] = {0, 0, 0, 0, 0};
+        if (r.mode == 0) {
+            cluster_barrier<G::C>();  // peers running before their shared memory is written
+#pragma unroll 1
+            for (int pass = 0; pass < G::R / G::RPP; ++pass) {
+                const int i = cx.crank * G::R + pass * G::RPP + grp;
+                float2 z[ER];
+#pragma unroll
+                for (int e = 0; e < ER; ++e)
+                    z[e] = __ldcg(reinterpret_cast<const float2*>(prm.chi + base + (size_t)i * W + 2 * (g + TR * e)));
+                row_forward<G>(cx, rs, i, g, gm, z);
+            }
+            cluster_barrier<G::C>();
+            columns_out_3d<G>(cx, r.a.spec, s);
+            continue;
+        }
+        columns_in_3d<G>(cx, r.a.spec, s);
+        cluster_barrier<G::C>();
+#pragma unroll 1
+        for (int pass = 0; pass < G::R / G::RPP; ++pass) {
+            const int i = cx.crank * G::R + pass * G::RPP + grp;
+            const size_t rowoff = base + (size_t)i * W;
+            float2 x[ER];
+            row_inverse<G>(cx, rs, i, g, gm, x);
+#pragma unroll
+            for (int e = 0; e < ER; ++e) {
+                const int j0 = 2 * (g + TR * e);
+                const size_t o = rowoff + j0;
+                const uchar2 mk2 = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o));
+                const double m[2] = {(double)mk2.x, (double)mk2.y};
+                const float2 qx = __ldcg(reinterpret_cast<const float2*>(prm.qx + o));
+                const float2 qy = __ldcg(reinterpret_cast<const float2*>(prm.qy + o));
+                const float2 qz = __ldcg(reinterpret_cast<const float2*>(prm.qz + o));
+                if (r.mode == 1) {
+                    const float2 f = __ldg(reinterpret_cast<const float2*>(prm.field + o));
+                    const float2 p = __ldcg(reinterpret_cast<const float2*>(prm.p + o));
+                    const float2 c = __ldcg(reinterpret_cast<const float2*>(prm.chi + o));
+                    const float cr = (j0 + 2 < W) ? __ldcg(prm.chi + o + 2) : c.y;
+                    const float2 cd = (i + 1 < H) ? __ldcg(reinterpret_cast<const float2*>(prm.chi + o + W)) : c;
+                    const float2 cz = (s + 1 < prm.S) ? __ldcg(reinterpret_cast<const float2*>(prm.chi + o + SL)) : c;
+                    float2 wv = make_float2((float)m[0], (float)m[1]);
+                    if (prm.weight) wv = __ldg(reinterpret_cast<const float2*>(prm.weight + o));
+                    const double w[2] = {wv.x, wv.y}, u[2] = {x[e].x, x[e].y}, ff[2] = {f.x, f.y};
+                    const double pp[2] = {p.x, p.y};
+                    const double gx[2] = {m[0] * ((double)c.y - c.x), m[1] * ((double)cr - c.y)};
+                    const double gy[2] = {m[0] * ((double)cd.x - c.x), m[1] * ((double)cd.y - c.y)};
+                    const double gz[2] = {m[0] * ((double)cz.x - c.x), m[1] * ((double)cz.y - c.y)};
+                    const double qxs[2] = {qx.x, qx.y}, qys[2] = {qy.x, qy.y}, qzs[2] = {qz.x, qz.y};
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const double res = w[t] * (u[t] - ff[t]);
+                        acc[0] += res * res;
+                        const double tvn = prm.tv_iso ? sqrt(gx[t] * gx[t] + gy[t] * gy[t] + gz[t] * gz[t])
+                                                      : fabs(gx[t]) + fabs(gy[t]) + fabs(gz[t]);
+                        acc[1] += tvn;
+                        const double d1 = pp[t] - lam * res;
+                        acc[2] += d1 * d1;
+                        acc[3] += tvn - (qxs[t] * gx[t] + qys[t] * gy[t] + qzs[t] * gz[t]);
+                    }
+                    x[e] = make_float2((float)(w[0] * p.x), (float)(w[1] * p.y));  // W p
+                } else {
+                    // G3^T M q: x, y as the per-slice report; z: (M qz)[s-1] - (M qz)[s][s < S-1]
+                    const double a0 = m[0] * qx.x, a1 = m[1] * qx.y;
+                    const double al = (j0 > 0) ? (double)__ldg(prm.mask + o - 1) * __ldcg(prm.qx + o - 1) : 0.0;
+                    const double a1r = (j0 + 2 < W) ? a1 : 0.0;
+                    double bu0 = 0.0, bu1 = 0.0, zu0 = 0.0, zu1 = 0.0;
+                    if (i > 0) {
+                        const uchar2 mu = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o - W));
+                        const float2 qu = __ldcg(reinterpret_cast<const float2*>(prm.qy + o - W));
+                        bu0 = (double)mu.x * qu.x;
+                        bu1 = (double)mu.y * qu.y;
+                    }
+                    if (s > 0) {
+                        const uchar2 mz = __ldg(reinterpret_cast<const uchar2*>(prm.mask + o - SL));
+                        const float2 qp = __ldcg(reinterpret_cast<const float2*>(prm.qz + o - SL));
+                        zu0 = (double)mz.x * qp.x;
+                        zu1 = (double)mz.y * qp.y;
+                    }
+                    const double b0 = (i + 1 < H) ? m[0] * qy.x : 0.0, b1 = (i + 1 < H) ? m[1] * qy.y : 0.0;
+                    const double z0 = (s + 1 < prm.S) ? m[0] * qz.x : 0.0, z1 = (s + 1 < prm.S) ? m[1] * qz.y : 0.0;
+                    const double k0 = (double)x[e].x + (al - a0) + (bu0 - b0) + (zu0 - z0);
+                    const double k1 = (double)x[e].y + (a0 - a1r) + (bu1 - b1) + (zu1 - z1);
+                    acc[4] += k0 * k0 + k1 * k1;
+                }
+            }
+            if (r.mode == 1) row_forward<G>(cx, rs, i, g, gm, x);
+        }
+        cluster_barrier<G::C>();  // all scatters in; all gathers done
+        if (r.mode == 1) columns_out_3d<G>(cx, r.a.spec, s);
+#pragma unroll
+        for (int t = 0; t < kReportSums; ++t) {
+            const double v = block_sum<G::NT>(acc[t], red);
+            if (threadIdx.x == 0 && ((r.mode == 1 && t < 4) || (r.mode == 2 && t == 4)))
+                r.partial[((size_t)s * G::C + cx.crank) * kReportSums + t] = v;
+        }
     }
 }
 

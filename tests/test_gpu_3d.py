@@ -106,3 +106,49 @@ def test_3d_edge_cases_and_errors():
         pcs.pcs_solve_volume_3d(g, torch.ones((32, 64, 64), dtype=torch.uint8, device="cuda"), -1.0, STEP, STEP, 5,
                                 torch.empty_like(g))
     assert ei.value.status == pcs.PCS_EINVAL
+
+
+@pytest.mark.parametrize("tv,weighted", [(0, False), (1, False), (0, True)])
+def test_report_3d_against_oracle(tv, weighted):
+    """FP64 diagnostics of the volume at (chi_N, p_N, q_N) against the oracle's, on the oracle's
+    own state after the same iterations.  Objective and residual come from chi, which agrees to
+    1e-4; the gap and the stationarity are differences of nearly equal terms, so they get a
+    looser bound plus an absolute floor from the terms' size."""
+    S, H, n_iter, lam = 32, 64, 120, 1.0
+    pb = phantoms.volume(H, H, S, seed=54, lam=lam, n_iter=n_iter)
+    w = phantoms.magnitude_weight(pb.mask, seed=55) if weighted else None
+    wd = None if w is None else w.astype(np.float64)
+    tvs = "iso" if tv else "aniso"
+    st = O3.pd_solve_3d(pb.field.astype(np.float64), pb.mask, lam, STEP, STEP, n_iter, weight=wd, tv=tvs,
+                        return_state=True)
+    ref = O3.diagnostics_3d(st, pb.field, pb.mask, lam, weight=wd, tv=tvs)
+    f = torch.from_numpy(np.ascontiguousarray(pb.field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.ascontiguousarray(pb.mask, dtype=np.uint8)).cuda()
+    wt = None if w is None else torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32)).cuda()
+    chi = torch.empty_like(f)
+    rep = pcs.pcs_solve_volume_3d(f, m, lam, STEP, STEP, n_iter, chi, tv=tv, weight=wt, report=True)
+    torch.cuda.synchronize()
+    assert rel_l2(chi.cpu().numpy(), st.chi) <= TOL
+    assert rep["iters"] == n_iter
+    assert rep["objective"] == pytest.approx(ref.primal, rel=1e-4)
+    assert rep["data_residual"] == pytest.approx(ref.data_residual, rel=1e-4)
+    assert rep["gap"] >= -1e-3 * ref.primal
+    assert abs(rep["gap"] - ref.gap) <= 2e-2 * ref.gap + 1e-4 * ref.primal
+    assert abs(rep["stationarity"] - ref.stationarity) <= 2e-2 * ref.stationarity + 1e-3
+
+
+def test_report_3d_at_zero_start():
+    """n_iter = 0: chi = p = q = 0, so objective = lambda/2 ||W dB||^2, gap = ||lambda W dB||^2 / (2 lambda),
+    stationarity 0, residual ||W dB|| (closed forms, no oracle)."""
+    pb = phantoms.volume(64, 64, 32, seed=56, lam=1.0, n_iter=1)
+    lam = 0.5
+    f = torch.from_numpy(np.ascontiguousarray(pb.field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.ascontiguousarray(pb.mask, dtype=np.uint8)).cuda()
+    chi = torch.empty_like(f)
+    rep = pcs.pcs_solve_volume_3d(f, m, lam, STEP, STEP, 0, chi, report=True)
+    torch.cuda.synchronize()
+    b2 = float(np.sum((pb.mask.astype(np.float64) * pb.field.astype(np.float32).astype(np.float64)) ** 2))
+    assert rep["objective"] == pytest.approx(0.5 * lam * b2, rel=1e-12)
+    assert rep["gap"] == pytest.approx(lam * b2 / 2.0, rel=1e-12)
+    assert rep["data_residual"] == pytest.approx(math.sqrt(b2), rel=1e-12)
+    assert rep["stationarity"] == 0.0
