@@ -250,6 +250,30 @@ PCS_API pcs_status pcs_field_map(const float *s0, const float *s1, size_t n_voxe
                                  double b0_tesla, double threshold, float *field_out, float *weight_out,
                                  unsigned char *mask_out, void *cuda_stream);
 
+/* ---------------------------------------------------------------- any slice size */
+
+/*
+ * pcs_solve_slices for slice sizes outside the compiled kernel variants, such
+ * as the 256 x 258 and 128 x 132 slices of the paper's acquisitions (Sec. III):
+ * any even H and W in [8, 512] whose prime factors are all <= 61.  Same
+ * problem and iteration as pcs_solve_slices (Eq. (1), Sec. II.A; 2-D D and G
+ * per slice, slices independent), with W = weight (NULL: W = mask) and M =
+ * mask as in pcs_solve_slices_weighted, tv as pcs_solve_volume_3d, and
+ * b0_axis 0 (B0 along y, the rows axis) or 1 (along x).  D(k) is evaluated
+ * in FP32 from the integer frequencies.  field, weight, chi_out: device float32
+ * [S][H][W]; mask: device uint8 [S][H][W]; 4-byte alignment suffices; chi_out
+ * must not alias field.  Allocates its scratch (4 floats and a half spectrum
+ * per pixel), frees it and synchronises cuda_stream before returning.
+ * Errors: PCS_EINVAL for bad arguments, PCS_EUNSUPPORTED for sizes outside
+ * the set above, PCS_ECUDA for CUDA failures.  S = 0 is a no-op.
+ */
+PCS_API pcs_status pcs_solve_slices_generic(const float *field, const unsigned char *mask, const float *weight,
+                                            int S, int H, int W, int b0_axis, double lambda, double tau,
+                                            double sigma, int n_iter, int tv, float *chi_out, void *cuda_stream);
+
+/* 1 if pcs_solve_slices_generic accepts H x W slices, else 0. */
+PCS_API int pcs_supported_generic(int H, int W);
+
 /* ---------------------------------------------------------------- 3-D variant */
 
 /*

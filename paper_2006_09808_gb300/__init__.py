@@ -152,6 +152,8 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_slices_weighted": (i, [vp, vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_volume_3d": (i, [vp, vp, vp, i, i, i, d, d, d, i, i, vp, ctypes.POINTER(pcs_slice_report), vp]),
         "pcs_supported_volume_3d": (i, [i, i, i]),
+        "pcs_solve_slices_generic": (i, [vp, vp, vp, i, i, i, i, d, d, d, i, i, vp, vp]),
+        "pcs_supported_generic": (i, [i, i]),
         "pcs_field_map": (i, [vp, vp, ctypes.c_size_t, d, d, d, vp, vp, vp, vp]),
         "pcs_check": (i, [vp]),
         "pcs_schedule_plan": (i, [i, i, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -303,6 +305,27 @@ def pcs_solve_volume_3d(field, mask, lam: float, tau: float, sigma: float, n_ite
                                               ctypes.byref(rep) if rep is not None else None, ctypes.c_void_p(st)),
            "pcs_solve_volume_3d")
     return rep.as_dict() if rep is not None else None
+
+
+def pcs_solve_slices_generic(field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, tv: int = 0,
+                             weight=None, b0_axis: int = 0, stream=None):
+    """Per-slice solve for any even H x W with prime factors <= 61 (field/mask/chi_out: [S][H][W]
+    float32/uint8/float32 CUDA tensors; weight: optional float32 data weighting W, default W = mask)."""
+    import torch
+
+    S, H, W = field.shape
+    f = _dev_ptr(field, "float32", (S, H, W), "field")
+    m = _dev_ptr(mask, "uint8", (S, H, W), "mask")
+    w = None if weight is None else _dev_ptr(weight, "float32", (S, H, W), "weight")
+    c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(load_library().pcs_solve_slices_generic(f, m, w, S, H, W, b0_axis, lam, tau, sigma, n_iter, tv, c,
+                                                   ctypes.c_void_p(st)),
+           "pcs_solve_slices_generic")
+
+
+def pcs_supported_generic(H: int, W: int) -> bool:
+    return bool(load_library().pcs_supported_generic(H, W))
 
 
 def pcs_field_map(s0, s1, t_shift_s: float, b0_tesla: float, threshold: float, field_out, weight_out, mask_out,

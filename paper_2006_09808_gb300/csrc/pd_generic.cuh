@@ -1,0 +1,305 @@
+// pd_generic.cuh -- the Sec. II.A iteration for slice sizes outside the
+// power-of-two / 3·2^k family: any even H x W whose lengths factor into
+// primes <= 61 (the paper's own 256 x 258 and 128 x 132 slices: 258 = 2·3·43,
+// 132 = 4·3·11).
+//
+// Per half step two launches, the half spectrum [S][H][W/2 + 1] (row-major,
+// complex) held in global memory between them:
+//   row kernel:    one warp per pair of rows; the two real rows travel as one
+//                  complex row (a + i b) through a length-W DFT in shared memory
+//                  -> the dual or primal row phase -> forward DFT, split back into
+//                  the two half-spectrum rows
+//   column kernel: one warp per spectrum column; length-H DFT x D(k)/(H W),
+//                  inverse DFT
+// The DFTs are mixed-radix Stockham passes with any radix: 2, 3, 4 as
+// butterflies, larger primes as a direct sum per output.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pd_cluster.cuh"
+
+namespace pcs {
+
+constexpr int kGenMaxStages = 12;
+constexpr int kGenRowWarps = 8;   // row pairs per CTA of the row kernel
+constexpr int kGenColTile = 16;   // spectrum columns per CTA of the column kernel
+
+struct GenPlan {
+    int n;                  // transform length
+    int nst;                // number of stages
+    int r[kGenMaxStages];   // radices, product n
+};
+
+struct GenParams {
+    const float* field;
+    const unsigned char* mask;
+    const float* weight;  // NULL: W = mask
+    float* chi;
+    float* chibar;
+    float* p;
+    float* qx;
+    float* qy;
+    float2* spec;          // [S][H][M1]
+    const float2* trow;    // exp(-2 pi i n / W), n < W
+    const float2* tcol;    // exp(-2 pi i n / H), n < H
+    GenPlan prow, pcol;
+    int S, H, W, M1;       // M1 = W / 2 + 1
+    float sigma, tau, inv_den;
+    int tv_iso;
+    int b0_axis;           // 0: B0 along y (rows), 1: along x
+    int phase;             // 0: dual step, 1: primal step
+    int store;             // 1: forward transforms of the phase's output to the spectrum
+};
+
+__device__ __forceinline__ float2 gcmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Length pl.n DFT by one warp in shared memory (unnormalised; inv: exponent sign +).
+// Input in a, b is scratch; returns the buffer holding the result.  Stage with
+// radix r after the radices so far multiply to Ns (R = n / r):
+//   X_out[(j / Ns) Ns r + k + q' Ns] = sum_q X_in[j + q R] w^(k q n/(Ns r)) w^(q q' R),
+// k = j mod Ns, w = exp(-+2 pi i / n), for j < R, q' < r.
+__device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan& pl, bool inv, int lane) {
+    const int N = pl.n;
+    const float sg = inv ? -1.f : 1.f;  // sign applied to the imaginary part of the forward twiddles
+    int Ns = 1;
+#pragma unroll 1
+    for (int st = 0; st < pl.nst; ++st) {
+        const int r = pl.r[st];
+        const int R = N / r;
+        const int step = N / (Ns * r);
+        if (r == 2) {
+#pragma unroll 1
+            for (int j = lane; j < R; j += 32) {
+                const int k = j % Ns;
+                float2 t = T[k * step];
+                t.y *= sg;
+                const float2 v0 = a[j], v1 = gcmul(a[j + R], t);
+                const int o = (j / Ns) * Ns * 2 + k;
+                b[o] = make_float2(v0.x + v1.x, v0.y + v1.y);
+                b[o + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+            }
+        } else if (r == 4) {
+#pragma unroll 1
+            for (int j = lane; j < R; j += 32) {
+                const int k = j % Ns;
+                float2 t1 = T[k * step], t2 = T[2 * k * step], t3 = T[3 * k * step];
+                t1.y *= sg;
+                t2.y *= sg;
+                t3.y *= sg;
+                const float2 v0 = a[j], v1 = gcmul(a[j + R], t1), v2 = gcmul(a[j + 2 * R], t2),
+                             v3 = gcmul(a[j + 3 * R], t3);
+                const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y), d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
+                const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y), d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
+                // -i d13 (forward) or +i d13 (inverse)
+                const float2 rd = make_float2(sg * d13.y, -sg * d13.x);
+                const int o = (j / Ns) * Ns * 4 + k;
+                b[o] = make_float2(s02.x + s13.x, s02.y + s13.y);
+                b[o + Ns] = make_float2(d02.x + rd.x, d02.y + rd.y);
+                b[o + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
+                b[o + 3 * Ns] = make_float2(d02.x - rd.x, d02.y - rd.y);
+            }
+        } else if (r == 3) {
+            const float h = 0.86602540378443865f;  // sin(2 pi / 3)
+#pragma unroll 1
+            for (int j = lane; j < R; j += 32) {
+                const int k = j % Ns;
+                float2 t1 = T[k * step], t2 = T[2 * k * step];
+                t1.y *= sg;
+                t2.y *= sg;
+                const float2 v0 = a[j], v1 = gcmul(a[j + R], t1), v2 = gcmul(a[j + 2 * R], t2);
+                const float2 s = make_float2(v1.x + v2.x, v1.y + v2.y), d = make_float2(v1.x - v2.x, v1.y - v2.y);
+                const float2 m = make_float2(v0.x - 0.5f * s.x, v0.y - 0.5f * s.y);
+                // -i h d (forward) or +i h d (inverse)
+                const float2 rd = make_float2(sg * h * d.y, -sg * h * d.x);
+                const int o = (j / Ns) * Ns * 3 + k;
+                b[o] = make_float2(v0.x + s.x, v0.y + s.y);
+                b[o + Ns] = make_float2(m.x + rd.x, m.y + rd.y);
+                b[o + 2 * Ns] = make_float2(m.x - rd.x, m.y - rd.y);
+            }
+        } else {
+            // larger prime: one output per lane iteration, the r terms summed directly
+#pragma unroll 1
+            for (int o = lane; o < N; o += 32) {
+                const int j = o % R, qp = o / R, k = j % Ns;
+                int c = k * step + qp * R;
+                if (c >= N) c -= N;
+                float2 acc = make_float2(0.f, 0.f);
+                int idx = 0;
+#pragma unroll 1
+                for (int q = 0; q < r; ++q) {
+                    float2 t = T[idx];
+                    t.y *= sg;
+                    const float2 v = a[j + q * R];
+                    acc.x = fmaf(v.x, t.x, fmaf(-v.y, t.y, acc.x));
+                    acc.y = fmaf(v.x, t.y, fmaf(v.y, t.x, acc.y));
+                    idx += c;
+                    if (idx >= N) idx -= N;
+                }
+                b[(j / Ns) * Ns * r + k + qp * Ns] = acc;
+            }
+        }
+        __syncwarp();
+        float2* t = a;
+        a = b;
+        b = t;
+        Ns *= r;
+    }
+    return a;
+}
+
+// Row kernel: a warp takes rows i0 = 2 pr, i1 = i0 + 1 of one slice.
+__global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = g.H, W = g.W, M1 = g.M1;
+    float2* T = reinterpret_cast<float2*>(smem_raw);
+    for (int t = threadIdx.x; t < W; t += blockDim.x) T[t] = g.trow[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = blockIdx.x * kGenRowWarps + warp;
+    if (pair >= g.S * (H / 2)) return;  // whole warps; no CTA barrier below
+    float2* bufa = T + W + (size_t)warp * 2 * W;
+    float2* bufb = bufa + W;
+    const int s = pair / (H / 2);
+    const int i0 = 2 * (pair - s * (H / 2)), i1 = i0 + 1;
+    const size_t r0 = ((size_t)s * H + i0) * W, r1 = r0 + W;
+    float2* sp0 = g.spec + ((size_t)s * H + i0) * M1;
+    float2* sp1 = sp0 + M1;
+
+    // z = a + i b from the two half-spectrum rows (Hermitian extension beyond M1)
+#pragma unroll 1
+    for (int k = lane; k < W; k += 32) {
+        float2 z;
+        if (k < M1) {
+            const float2 A = __ldcg(sp0 + k), B = __ldcg(sp1 + k);
+            z = make_float2(A.x - B.y, A.y + B.x);
+        } else {
+            const float2 A = __ldcg(sp0 + (W - k)), B = __ldcg(sp1 + (W - k));
+            z = make_float2(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+        }
+        bufa[k] = z;
+    }
+    __syncwarp();
+    float2* u = warp_dft(bufa, bufb, T, g.prow, true, lane);
+    float2* o = (u == bufa) ? bufb : bufa;
+    const float sigma = g.sigma, tau = g.tau;
+    if (g.phase == 0) {
+        // dual step at both rows (Sec. II.A): p and q from u = D chibar and chibar's differences
+        const bool down1 = (i1 + 1 < H);
+#pragma unroll 1
+        for (int n = lane; n < W; n += 32) {
+            const float2 uv = u[n];
+            const bool right = (n + 1 < W);
+            const size_t a0 = r0 + n, a1 = r1 + n;
+            const float c0 = __ldcg(g.chibar + a0), c1 = __ldcg(g.chibar + a1);
+            const float c0r = right ? __ldcg(g.chibar + a0 + 1) : c0;
+            const float c1r = right ? __ldcg(g.chibar + a1 + 1) : c1;
+            const float c2 = down1 ? __ldcg(g.chibar + a1 + W) : c1;
+            const float m0 = (float)__ldg(g.mask + a0), m1 = (float)__ldg(g.mask + a1);
+            const float w0 = g.weight ? __ldg(g.weight + a0) : m0;
+            const float w1 = g.weight ? __ldg(g.weight + a1) : m1;
+            const float p0 = (__ldcg(g.p + a0) + sigma * (w0 * (uv.x - __ldg(g.field + a0)))) * g.inv_den;
+            const float p1 = (__ldcg(g.p + a1) + sigma * (w1 * (uv.y - __ldg(g.field + a1)))) * g.inv_den;
+            float qx0 = __ldcg(g.qx + a0) + sigma * m0 * (c0r - c0);
+            float qy0 = __ldcg(g.qy + a0) + sigma * m0 * (c1 - c0);
+            float qx1 = __ldcg(g.qx + a1) + sigma * m1 * (c1r - c1);
+            float qy1 = __ldcg(g.qy + a1) + sigma * m1 * (c2 - c1);
+            tv_prox(qx0, qy0, g.tv_iso);
+            tv_prox(qx1, qy1, g.tv_iso);
+            __stcg(g.p + a0, p0);
+            __stcg(g.p + a1, p1);
+            __stcg(g.qx + a0, qx0);
+            __stcg(g.qy + a0, qy0);
+            __stcg(g.qx + a1, qx1);
+            __stcg(g.qy + a1, qy1);
+            o[n] = make_float2(w0 * p0, w1 * p1);  // W p, transformed next
+        }
+    } else {
+        // primal step: chi+ = chi - tau (v + G^T q), v = D W p; chibar = 2 chi+ - chi.
+        // q is zero wherever the 0/1 mask is (zero start, masked increments), so M q = q.
+        const bool up0 = (i0 > 0), down1 = (i1 + 1 < H);
+#pragma unroll 1
+        for (int n = lane; n < W; n += 32) {
+            const float2 vv = u[n];
+            const size_t a0 = r0 + n, a1 = r1 + n;
+            const float qx0 = __ldcg(g.qx + a0), qx1 = __ldcg(g.qx + a1);
+            const float qy0 = __ldcg(g.qy + a0), qy1 = __ldcg(g.qy + a1);
+            const float qxl0 = (n > 0) ? __ldcg(g.qx + a0 - 1) : 0.f;
+            const float qxl1 = (n > 0) ? __ldcg(g.qx + a1 - 1) : 0.f;
+            const float qyu0 = up0 ? __ldcg(g.qy + a0 - W) : 0.f;
+            const bool last_col = (n + 1 == W);
+            const float d0 = (qxl0 - (last_col ? 0.f : qx0)) + (qyu0 - qy0);  // row i0 < H - 1
+            const float d1 = (qxl1 - (last_col ? 0.f : qx1)) + (qy0 - (down1 ? qy1 : 0.f));
+            const float c0 = __ldcg(g.chi + a0), c1 = __ldcg(g.chi + a1);
+            const float n0 = c0 - tau * vv.x - tau * d0;
+            const float n1 = c1 - tau * vv.y - tau * d1;
+            __stcg(g.chi + a0, n0);
+            __stcg(g.chi + a1, n1);
+            const float b0 = 2.f * n0 - c0, b1 = 2.f * n1 - c1;
+            __stcg(g.chibar + a0, b0);
+            __stcg(g.chibar + a1, b1);
+            o[n] = make_float2(b0, b1);
+        }
+    }
+    __syncwarp();
+    if (g.phase == 0 || g.store) {
+        float2* Z = warp_dft(o, u, T, g.prow, false, lane);
+        // split: A = (Z(k) + conj Z(-k)) / 2, B = (Z(k) - conj Z(-k)) / (2 i)
+#pragma unroll 1
+        for (int k = lane; k < M1; k += 32) {
+            const float2 zk = Z[k], zm = Z[k == 0 ? 0 : W - k];
+            __stcg(sp0 + k, make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y)));
+            __stcg(sp1 + k, make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x)));
+        }
+    }
+}
+
+__device__ __forceinline__ float gen_freq(int k, int n) { return (float)(k < (n + 1) / 2 ? k : k - n) / (float)n; }
+
+// Column kernel: CTA (tile of kGenColTile spectrum columns, slice); one warp per column.
+__global__ void __launch_bounds__(kGenColTile * 32) gen_cols_kernel(GenParams g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = g.H, W = g.W, M1 = g.M1;
+    float2* T = reinterpret_cast<float2*>(smem_raw);
+    float2* cols = T + H;  // [kGenColTile][2][H]
+    const int kx0 = blockIdx.x * kGenColTile, s = blockIdx.y;
+    const int ncol = min(kGenColTile, M1 - kx0);
+    float2* spec = g.spec + (size_t)s * H * M1;
+    for (int t = threadIdx.x; t < H; t += blockDim.x) T[t] = g.tcol[t];
+    // rows of the tile: adjacent threads take adjacent columns
+#pragma unroll 1
+    for (int t = threadIdx.x; t < H * kGenColTile; t += blockDim.x) {
+        const int c = t % kGenColTile, ky = t / kGenColTile;
+        if (c < ncol) cols[(size_t)c * 2 * H + ky] = __ldcg(spec + (size_t)ky * M1 + kx0 + c);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < ncol) {
+        const int kx = kx0 + warp;
+        float2* a = cols + (size_t)warp * 2 * H;
+        float2* b = a + H;
+        float2* X = warp_dft(a, b, T, g.pcol, false, lane);
+        const float fx = (float)kx / (float)W;
+        const float scale = 1.0f / ((float)H * (float)W);
+#pragma unroll 1
+        for (int ky = lane; ky < H; ky += 32) {
+            const float fy = gen_freq(ky, H);
+            const float k2 = fx * fx + fy * fy;
+            const float fb = g.b0_axis ? fx : fy;
+            const float d = (k2 > 0.f) ? (1.0f / 3.0f - (fb * fb) / k2) * scale : 0.f;
+            X[ky] = make_float2(X[ky].x * d, X[ky].y * d);
+        }
+        __syncwarp();
+        warp_dft(X, X == a ? b : a, T, g.pcol, true, lane);  // 2 nst stages in all: result back in a
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int t = threadIdx.x; t < H * kGenColTile; t += blockDim.x) {
+        const int c = t % kGenColTile, ky = t / kGenColTile;
+        if (c < ncol) __stcg(spec + (size_t)ky * M1 + kx0 + c, cols[(size_t)c * 2 * H + ky]);
+    }
+}
+
+}  // namespace pcs

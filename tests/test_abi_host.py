@@ -69,6 +69,20 @@ def test_host_side_argument_checks(lib):
     lib.pcs_destroy(None)  # NULL-safe
 
 
+def test_generic_size_rule(lib):
+    # even H and W in [8, 512] whose prime factors are <= 61 (the paper's 256 x 258, 128 x 132)
+    for H, W in ((256, 258), (128, 132), (8, 8), (512, 512), (90, 98), (122, 8)):
+        assert lib.pcs_supported_generic(H, W) == 1, (H, W)
+    for H, W in ((256, 134), (9, 12), (6, 12), (514, 8), (8, 2 * 67), (0, 8)):
+        assert lib.pcs_supported_generic(H, W) == 0, (H, W)
+    gs = lib.pcs_solve_slices_generic
+    assert gs(None, None, None, 2, 256, 134, 0, 1.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_EUNSUPPORTED
+    assert gs(None, None, None, 2, 256, 258, 0, 1.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_EINVAL  # NULL
+    assert gs(None, None, None, 0, 256, 258, 0, 1.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_OK  # S = 0
+    assert gs(None, None, None, 1, 256, 258, 2, 1.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_EINVAL  # b0_axis
+    assert gs(None, None, None, 1, 256, 258, 0, 0.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_EINVAL  # lambda
+
+
 def test_create_without_gpu_reports_cuda_error(lib):
     import torch
 

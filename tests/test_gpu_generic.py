@@ -1,0 +1,143 @@
+"""Any-size per-slice solver (pcs_solve_slices_generic) against the FP64 oracle.
+
+Sizes include the paper's own slices, 256 x 258 and 128 x 132 (FFT lengths with the
+prime factors 43 and 11), rectangles, and the smallest accepted size.  tau = sigma =
+1/sqrt(4/9 + 8), a valid step for every 0/1 mask (||D|| <= 2/3, ||G||^2 <= 8).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2006_09808_gb300 as pcs  # noqa: E402
+import phantoms  # noqa: E402
+from oracle import pd_oracle as O  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+STEP = 1.0 / math.sqrt(4.0 / 9.0 + 8.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_09808_gb300 import build
+
+    build.build()
+    pcs.load_library()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_generic(field, mask, lam, n_iter, tv=0, weight=None, b0_axis=0):
+    f = torch.from_numpy(np.ascontiguousarray(field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint8)).cuda()
+    w = None if weight is None else torch.from_numpy(np.ascontiguousarray(weight, dtype=np.float32)).cuda()
+    chi = torch.full_like(f, float("nan"))
+    pcs.pcs_solve_slices_generic(f, m, lam, STEP, STEP, n_iter, chi, tv=tv, weight=w, b0_axis=b0_axis)
+    torch.cuda.synchronize()
+    return chi.cpu().numpy()
+
+
+def oracle(field, mask, lam, n_iter, tv=0, weight=None, b0_axis=0):
+    return O.pd_solve(np.asarray(field, np.float64), mask, lam, STEP, STEP, n_iter, b0_axis=b0_axis,
+                      weight=None if weight is None else np.asarray(weight, np.float64),
+                      tv="iso" if tv else "aniso")
+
+
+@pytest.mark.parametrize(
+    "S,H,W,n_iter,lam,tv,b0",
+    [
+        (4, 256, 258, 60, 1.0, 0, 0),   # the stent slices' shape
+        (6, 128, 132, 100, 1.0, 0, 0),  # the seed / needle slices' shape
+        (3, 128, 132, 100, 1.0, 1, 0),
+        (3, 128, 132, 80, 5e-4, 0, 1),
+        (2, 90, 98, 80, 1.0, 0, 0),     # 2·3²·5 x 2·7²
+        (5, 30, 42, 150, 1.0, 1, 1),
+        (2, 64, 64, 80, 1.0, 0, 0),     # power of two: the same problem as the compiled variants
+    ],
+)
+def test_parity_generic(S, H, W, n_iter, lam, tv, b0):
+    pb = phantoms.volume(H, W, S, seed=61 + H + W, lam=lam, n_iter=n_iter)
+    ref = oracle(pb.field, pb.mask, lam, n_iter, tv=tv, b0_axis=b0)
+    got = gpu_generic(pb.field, pb.mask, lam, n_iter, tv=tv, b0_axis=b0)
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, ref) <= TOL
+    for s in range(S):
+        assert rel_l2(got[s], ref[s]) <= 10 * TOL, s
+    m = pb.mask.astype(bool)
+    assert rel_l2(got[m], ref[m]) <= TOL
+
+
+def test_generic_weighted_and_batch_independence():
+    pb = phantoms.volume(128, 132, 4, seed=71, lam=1.0, n_iter=60)
+    w = phantoms.magnitude_weight(pb.mask, seed=72)
+    ref = oracle(pb.field, pb.mask, 1.0, 60, weight=w)
+    got = gpu_generic(pb.field, pb.mask, 1.0, 60, weight=w)
+    assert rel_l2(got, ref) <= TOL
+    # a slice alone equals the same slice inside the batch, bit for bit
+    alone = gpu_generic(pb.field[2:3], pb.mask[2:3], 1.0, 60, weight=w[2:3])
+    assert np.array_equal(alone[0], got[2])
+
+
+def test_generic_full_stent_shape():
+    """256 x 258 x 25, the stent acquisition's shape, 20 iterations against the oracle."""
+    pb = phantoms.volume(256, 258, 25, seed=73, lam=5e-4, n_iter=20)
+    ref = oracle(pb.field, pb.mask, pb.lam, 20)
+    got = gpu_generic(pb.field, pb.mask, pb.lam, 20)
+    assert rel_l2(got, ref) <= TOL
+
+
+def test_generic_matches_compiled_variant_at_64():
+    """At 64 x 64 both solvers take the same problem: results agree to rounding."""
+    pb = phantoms.volume(64, 64, 3, seed=74, lam=1.0, n_iter=50)
+    got = gpu_generic(pb.field, pb.mask, 1.0, 50)
+    f = torch.from_numpy(pb.field.astype(np.float32)).cuda()
+    m = torch.from_numpy(pb.mask.astype(np.uint8)).cuda()
+    chi = torch.empty_like(f)
+    ctx = pcs.pcs_create(64, 64, 3)
+    try:
+        pcs.pcs_solve_slices(ctx, f, m, 1.0, STEP, STEP, 50, chi)
+        torch.cuda.synchronize()
+    finally:
+        pcs.pcs_destroy(ctx)
+    assert rel_l2(got, chi.cpu().numpy()) <= 1e-5
+
+
+def test_generic_edge_cases_and_errors():
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((2, 8, 12)).astype(np.float32)
+    ones = np.ones_like(f, dtype=np.uint8)
+    assert np.all(gpu_generic(f, ones, 1.0, 0) == 0)                   # n_iter = 0
+    assert np.all(gpu_generic(f, np.zeros_like(ones), 1.0, 30) == 0)   # empty mask
+    one = gpu_generic(f, ones, 1.0, 1)                                  # smallest size, one iteration
+    assert rel_l2(one, oracle(f, ones, 1.0, 1)) <= 1e-6
+    assert rel_l2(gpu_generic(f, ones, 1.0, 200), oracle(f, ones, 1.0, 200)) <= TOL
+    assert pcs.pcs_supported_generic(256, 258) and pcs.pcs_supported_generic(128, 132)
+    e0 = torch.zeros((0, 8, 12), device="cuda")
+    pcs.pcs_solve_slices_generic(e0, torch.zeros((0, 8, 12), dtype=torch.uint8, device="cuda"), 1.0, STEP, STEP,
+                                 5, torch.empty_like(e0))  # S = 0: no-op
+    for shape, status in (((2, 8, 134), pcs.PCS_EUNSUPPORTED), ((2, 9, 12), pcs.PCS_EUNSUPPORTED),
+                          ((1, 8, 514), pcs.PCS_EUNSUPPORTED)):
+        g = torch.zeros(shape, device="cuda")
+        with pytest.raises(pcs.PcsError) as ei:
+            pcs.pcs_solve_slices_generic(g, torch.ones(shape, dtype=torch.uint8, device="cuda"), 1.0, STEP, STEP,
+                                         5, torch.empty_like(g))
+        assert ei.value.status == status, shape
+    g = torch.zeros((1, 8, 12), device="cuda")
+    mk = torch.ones((1, 8, 12), dtype=torch.uint8, device="cuda")
+    for kw in (dict(lam=-1.0), dict(tv=2), dict(b0_axis=2)):
+        args = dict(lam=1.0, tv=0, b0_axis=0)
+        args.update(kw)
+        with pytest.raises(pcs.PcsError) as ei:
+            pcs.pcs_solve_slices_generic(g, mk, args["lam"], STEP, STEP, 5, torch.empty_like(g), tv=args["tv"],
+                                         b0_axis=args["b0_axis"])
+        assert ei.value.status == pcs.PCS_EINVAL

@@ -151,7 +151,7 @@ def test_sphere_field_closed_form():
 # --------------------------------------------------------------------------- dense brute force of the operators
 
 
-@pytest.mark.parametrize("H,W", [(4, 4), (5, 6), (6, 8), (3, 7)])
+@pytest.mark.parametrize("H,W", [(4, 4), (5, 6), (6, 8), (3, 7), (4, 22), (2, 86)])
 def test_apply_D_matches_dense_dft(H, W):
     rng = np.random.default_rng(H * 100 + W)
     Dk = O.dipole_kernel(H, W)
