@@ -464,6 +464,109 @@ def run_volume3d(args):
     return 0
 
 
+NATIVE_H, NATIVE_W, NATIVE_S = 256, 258, 25
+STEP_2D_SAFE = 1.0 / (4.0 / 9.0 + 8.0) ** 0.5  # ||K|| <= sqrt(4/9 + 8) for every 0/1 mask
+
+
+def run_native_shape(args):
+    """Any-size path on the stent acquisition's slice shape, 256 x 258 x 25: one
+    pcs_solve_slices_generic call per step (500 iterations)."""
+    import numpy as np
+    import torch
+
+    import paper_2006_09808_gb300 as pcs
+    import phantoms
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pcs.load_library()
+    pb = phantoms.volume(NATIVE_H, NATIVE_W, NATIVE_S, seed=rank, lam=LAM, n_iter=N_ITER, name="bench258")
+    field = torch.from_numpy(pb.field).to(dev)
+    mask = torch.from_numpy(pb.mask).to(dev)
+    chi = torch.empty_like(field)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        pcs.pcs_solve_slices_generic(field, mask, LAM, STEP_2D_SAFE, STEP_2D_SAFE, N_ITER, chi, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    ms_step = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    work = NATIVE_S * NATIVE_H * NATIVE_W * N_ITER
+    hf = torch.from_numpy(pb.field).pin_memory()
+    hm = torch.from_numpy(pb.mask).pin_memory()
+    hc = torch.empty(pb.field.shape, dtype=torch.float32).pin_memory()
+    e2e = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        field.copy_(hf, non_blocking=True)
+        mask.copy_(hm, non_blocking=True)
+        step()
+        hc.copy_(chi, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    assert torch.equal(hc, chi.cpu())
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        hbm_peak = float(peaks["hbm_gbs"])
+        achieved = ALG_BYTES_PER_VOXEL_ITER * work / (ms_step * 1e-3) / 1e9
+        line = {
+            "metric": "PD voxel-iterations/s (256x258 slices)",
+            "value": work / (ms_step * 1e-3),
+            "unit": "voxel-iter/s",
+            "n_gpus": 1,
+            "steps": args.steps,
+            "warmup": max(args.warmup, 3),
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "the stent acquisition's shape: 25 slices of 256x258 (row FFT length 258 = "
+                                   "2*3*43), 500 PD iterations, lambda=5e-4", "H": NATIVE_H, "W": NATIVE_W,
+                       "slices": NATIVE_S, "n_iter": N_ITER, "tau_sigma": STEP_2D_SAFE,
+                       "l2": "flushed between steps (256 MiB device write)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "alg_bytes_per_voxel_iter": ALG_BYTES_PER_VOXEL_ITER},
+            "e2e": {"value": work / (sum(e2e) / len(e2e)), "unit": "voxel-iter/s",
+                    "h2d_bytes_per_step": int(pb.field.nbytes + pb.mask.nbytes),
+                    "d2h_bytes_per_step": int(pb.field.nbytes)},
+            "gpu_launches": args.steps * (4 * N_ITER - 1),
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            from oracle import pd_oracle as O  # cpu_baseline leg only
+
+            n_it = 20
+            t0 = time.perf_counter()
+            O.pd_solve(pb.field.astype(np.float64), pb.mask, LAM, STEP_2D_SAFE, STEP_2D_SAFE, n_it)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": work / N_ITER * n_it / dt, "unit": "voxel-iter/s", "cores": 1,
+                                    "kind": "oracle",
+                                    "sample": f"all 25 slices x {n_it} iterations ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_fieldmap(args):
     """Field-map preprocessing (pcs_field_map) of the 256 x 256 x 64 volume's two acquisitions."""
     import torch
@@ -637,9 +740,10 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
     ap.add_argument("--plain-loop", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the plain per-slice GPU loop (one timed volume)")
-    ap.add_argument("--workload", choices=["volume", "serve", "volume3d", "fieldmap"], default="volume",
+    ap.add_argument("--workload", choices=["volume", "serve", "volume3d", "fieldmap", "native"], default="volume",
                     help="volume: the 256x256x64 solve (default); serve: the serving loop; "
-                         "volume3d: the 3-D variant on the same volume; fieldmap: the preprocessing step")
+                         "volume3d: the 3-D variant on the same volume; fieldmap: the preprocessing step; "
+                         "native: the any-size path on 25 slices of 256x258")
     ap.add_argument("--requests", type=int, default=80, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
     ap.add_argument("--baseline-requests", type=int, default=20, help="serving: requests in the plain baseline")
@@ -652,6 +756,8 @@ def main():
         return run_volume3d(args)
     if args.workload == "fieldmap":
         return run_fieldmap(args)
+    if args.workload == "native":
+        return run_native_shape(args)
     return run_native(args)
 
 

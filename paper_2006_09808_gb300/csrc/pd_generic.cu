@@ -56,7 +56,7 @@ pcs_status failg(pcs_status st, const char* what, cudaError_t e = cudaSuccess) {
 }
 
 size_t rows_smem(int W) { return sizeof(float2) * (size_t)W * (1 + 2 * pcs::kGenRowWarps); }
-size_t cols_smem(int H) { return sizeof(float2) * (size_t)H * (1 + 2 * pcs::kGenColTile); }
+size_t cols_smem(int H) { return sizeof(float2) * ((size_t)H + (size_t)(2 * H + 1) * pcs::kGenColTile); }
 
 }  // namespace
 

@@ -11,8 +11,8 @@
 //                  the two half-spectrum rows
 //   column kernel: one warp per spectrum column; length-H DFT x D(k)/(H W),
 //                  inverse DFT
-// The DFTs are mixed-radix Stockham passes with any radix: 2, 3, 4 as
-// butterflies, larger primes as a direct sum per output.
+// The DFTs are mixed-radix Stockham passes: 2, 3, 4 as butterflies, larger odd
+// primes as a symmetric direct DFT (terms q and r - q paired).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -57,7 +57,8 @@ __device__ __forceinline__ float2 gcmul(float2 a, float2 b) {
 }
 
 // Length pl.n DFT by one warp in shared memory (unnormalised; inv: exponent sign +).
-// Input in a, b is scratch; returns the buffer holding the result.  Stage with
+// Input in a, b is scratch; returns the buffer holding the result (which one depends
+// on the plan's radices).  Stage with
 // radix r after the radices so far multiply to Ns (R = n / r):
 //   X_out[(j / Ns) Ns r + k + q' Ns] = sum_q X_in[j + q R] w^(k q n/(Ns r)) w^(q q' R),
 // k = j mod Ns, w = exp(-+2 pi i / n), for j < R, q' < r.
@@ -120,26 +121,66 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
                 b[o + 2 * Ns] = make_float2(m.x - rd.x, m.y - rd.y);
             }
         } else {
-            // larger prime: one output per lane iteration, the r terms summed directly
+            // odd prime r >= 5: (1) pre-twiddle in place; (2) sums s_q = v_q + v_(r-q) and
+            // differences d_q = v_q - v_(r-q) into b; (3) outputs q' and r - q' together:
+            // A = v_0 + sum s_q cos(2 pi m / r), B = sum d_q (-sin(2 pi m / r)), m = q q' mod r,
+            // X_q' = A + i sg B, X_(r-q') = A - i sg B (forward sg = 1).  The result lands in a.
 #pragma unroll 1
-            for (int o = lane; o < N; o += 32) {
-                const int j = o % R, qp = o / R, k = j % Ns;
-                int c = k * step + qp * R;
-                if (c >= N) c -= N;
-                float2 acc = make_float2(0.f, 0.f);
-                int idx = 0;
-#pragma unroll 1
-                for (int q = 0; q < r; ++q) {
-                    float2 t = T[idx];
-                    t.y *= sg;
-                    const float2 v = a[j + q * R];
-                    acc.x = fmaf(v.x, t.x, fmaf(-v.y, t.y, acc.x));
-                    acc.y = fmaf(v.x, t.y, fmaf(v.y, t.x, acc.y));
-                    idx += c;
-                    if (idx >= N) idx -= N;
-                }
-                b[(j / Ns) * Ns * r + k + qp * Ns] = acc;
+            for (int u = lane + R; u < N; u += 32) {
+                const int j = u % R, q = u / R;
+                float2 t = T[(j % Ns) * step * q];
+                t.y *= sg;
+                a[u] = gcmul(a[u], t);
             }
+            __syncwarp();
+            const int h = (r - 1) / 2;
+#pragma unroll 1
+            for (int u = lane; u < R * (h + 1); u += 32) {
+                const int j = u % R, q = u / R;
+                if (q == 0) {
+                    b[j] = a[j];
+                } else {
+                    const float2 x = a[j + q * R], y = a[j + (r - q) * R];
+                    b[j + q * R] = make_float2(x.x + y.x, x.y + y.y);
+                    b[j + (r - q) * R] = make_float2(x.x - y.x, x.y - y.y);
+                }
+            }
+            __syncwarp();
+#pragma unroll 1
+            for (int u = lane; u < R * (h + 1); u += 32) {
+                const int j = u % R, qp = u / R, k = j % Ns;
+                const int ob = (j / Ns) * Ns * r + k;
+                const float2 v0 = b[j];
+                if (qp == 0) {
+                    float2 acc = v0;
+#pragma unroll 1
+                    for (int q = 1; q <= h; ++q) {
+                        const float2 sq = b[j + q * R];
+                        acc.x += sq.x;
+                        acc.y += sq.y;
+                    }
+                    a[ob] = acc;
+                } else {
+                    float2 A = v0, B = make_float2(0.f, 0.f);
+                    int m = 0;
+#pragma unroll 1
+                    for (int q = 1; q <= h; ++q) {
+                        m += qp;
+                        if (m >= r) m -= r;
+                        const float2 cs = T[m * R];  // (cos, -sin) of 2 pi m / r
+                        const float2 sq = b[j + q * R], dq = b[j + (r - q) * R];
+                        A.x = fmaf(sq.x, cs.x, A.x);
+                        A.y = fmaf(sq.y, cs.x, A.y);
+                        B.x = fmaf(dq.x, cs.y, B.x);
+                        B.y = fmaf(dq.y, cs.y, B.y);
+                    }
+                    a[ob + qp * Ns] = make_float2(A.x - sg * B.y, A.y + sg * B.x);
+                    a[ob + (r - qp) * Ns] = make_float2(A.x + sg * B.y, A.y - sg * B.x);
+                }
+            }
+            __syncwarp();
+            Ns *= r;
+            continue;  // result in a: no swap
         }
         __syncwarp();
         float2* t = a;
@@ -259,26 +300,32 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
 __device__ __forceinline__ float gen_freq(int k, int n) { return (float)(k < (n + 1) / 2 ? k : k - n) / (float)n; }
 
 // Column kernel: CTA (tile of kGenColTile spectrum columns, slice); one warp per column.
+// Column c's two buffers start at c (2H + 1): the odd stride puts the tile's
+// columns on distinct banks for the row-wise load and store.
 __global__ void __launch_bounds__(kGenColTile * 32) gen_cols_kernel(GenParams g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = g.H, W = g.W, M1 = g.M1;
+    const int CS = 2 * H + 1;
     float2* T = reinterpret_cast<float2*>(smem_raw);
-    float2* cols = T + H;  // [kGenColTile][2][H]
+    float2* cols = T + H;  // [kGenColTile][CS]
     const int kx0 = blockIdx.x * kGenColTile, s = blockIdx.y;
     const int ncol = min(kGenColTile, M1 - kx0);
     float2* spec = g.spec + (size_t)s * H * M1;
     for (int t = threadIdx.x; t < H; t += blockDim.x) T[t] = g.tcol[t];
     // rows of the tile: adjacent threads take adjacent columns
-#pragma unroll 1
-    for (int t = threadIdx.x; t < H * kGenColTile; t += blockDim.x) {
-        const int c = t % kGenColTile, ky = t / kGenColTile;
-        if (c < ncol) cols[(size_t)c * 2 * H + ky] = __ldcg(spec + (size_t)ky * M1 + kx0 + c);
+    const int c = threadIdx.x % kGenColTile;
+    const int ky0 = threadIdx.x / kGenColTile;
+    constexpr int KY_STEP = kGenColTile * 32 / kGenColTile;  // rows per sweep of the CTA
+    if (c < ncol) {
+        const float2* src = spec + kx0 + c;
+#pragma unroll 4
+        for (int ky = ky0; ky < H; ky += KY_STEP) cols[(size_t)c * CS + ky] = __ldcg(src + (size_t)ky * M1);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (warp < ncol) {
         const int kx = kx0 + warp;
-        float2* a = cols + (size_t)warp * 2 * H;
+        float2* a = cols + (size_t)warp * CS;
         float2* b = a + H;
         float2* X = warp_dft(a, b, T, g.pcol, false, lane);
         const float fx = (float)kx / (float)W;
@@ -292,13 +339,14 @@ __global__ void __launch_bounds__(kGenColTile * 32) gen_cols_kernel(GenParams g)
             X[ky] = make_float2(X[ky].x * d, X[ky].y * d);
         }
         __syncwarp();
-        warp_dft(X, X == a ? b : a, T, g.pcol, true, lane);  // 2 nst stages in all: result back in a
+        // both directions swap the buffers equally often: the result is back in a
+        warp_dft(X, X == a ? b : a, T, g.pcol, true, lane);
     }
     __syncthreads();
-#pragma unroll 1
-    for (int t = threadIdx.x; t < H * kGenColTile; t += blockDim.x) {
-        const int c = t % kGenColTile, ky = t / kGenColTile;
-        if (c < ncol) __stcg(spec + (size_t)ky * M1 + kx0 + c, cols[(size_t)c * 2 * H + ky]);
+    if (c < ncol) {
+        float2* dst = spec + kx0 + c;
+#pragma unroll 4
+        for (int ky = ky0; ky < H; ky += KY_STEP) __stcg(dst + (size_t)ky * M1, cols[(size_t)c * CS + ky]);
     }
 }
 
