@@ -146,36 +146,54 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
                 }
             }
             __syncwarp();
+            // q' = 0: X_0 = v_0 + sum s_q
 #pragma unroll 1
-            for (int u = lane; u < R * (h + 1); u += 32) {
-                const int j = u % R, qp = u / R, k = j % Ns;
-                const int ob = (j / Ns) * Ns * r + k;
-                const float2 v0 = b[j];
-                if (qp == 0) {
-                    float2 acc = v0;
+            for (int j = lane; j < R; j += 32) {
+                float2 acc = b[j];
 #pragma unroll 1
-                    for (int q = 1; q <= h; ++q) {
-                        const float2 sq = b[j + q * R];
-                        acc.x += sq.x;
-                        acc.y += sq.y;
-                    }
-                    a[ob] = acc;
-                } else {
-                    float2 A = v0, B = make_float2(0.f, 0.f);
-                    int m = 0;
+                for (int q = 1; q <= h; ++q) {
+                    const float2 sq = b[j + q * R];
+                    acc.x += sq.x;
+                    acc.y += sq.y;
+                }
+                a[(j / Ns) * Ns * r + j % Ns] = acc;
+            }
+            // q' = 1..h: two (j, q') units per lane at a time (independent chains)
+            const int NU = R * h;
 #pragma unroll 1
-                    for (int q = 1; q <= h; ++q) {
-                        m += qp;
-                        if (m >= r) m -= r;
-                        const float2 cs = T[m * R];  // (cos, -sin) of 2 pi m / r
-                        const float2 sq = b[j + q * R], dq = b[j + (r - q) * R];
-                        A.x = fmaf(sq.x, cs.x, A.x);
-                        A.y = fmaf(sq.y, cs.x, A.y);
-                        B.x = fmaf(dq.x, cs.y, B.x);
-                        B.y = fmaf(dq.y, cs.y, B.y);
-                    }
-                    a[ob + qp * Ns] = make_float2(A.x - sg * B.y, A.y + sg * B.x);
-                    a[ob + (r - qp) * Ns] = make_float2(A.x + sg * B.y, A.y - sg * B.x);
+            for (int u0 = lane; u0 < NU; u0 += 64) {
+                const bool has1 = (u0 + 32 < NU);
+                const int u1 = has1 ? u0 + 32 : u0;
+                const int j0 = u0 % R, qp0 = 1 + u0 / R;
+                const int j1 = u1 % R, qp1 = 1 + u1 / R;
+                float2 A0 = b[j0], B0 = make_float2(0.f, 0.f);
+                float2 A1 = b[j1], B1 = make_float2(0.f, 0.f);
+                int m0 = 0, m1 = 0;
+#pragma unroll 1
+                for (int q = 1; q <= h; ++q) {
+                    m0 += qp0;
+                    if (m0 >= r) m0 -= r;
+                    m1 += qp1;
+                    if (m1 >= r) m1 -= r;
+                    const float2 c0 = T[m0 * R], c1 = T[m1 * R];  // (cos, -sin) of 2 pi m / r
+                    const float2 s0 = b[j0 + q * R], d0 = b[j0 + (r - q) * R];
+                    const float2 s1 = b[j1 + q * R], d1 = b[j1 + (r - q) * R];
+                    A0.x = fmaf(s0.x, c0.x, A0.x);
+                    A0.y = fmaf(s0.y, c0.x, A0.y);
+                    B0.x = fmaf(d0.x, c0.y, B0.x);
+                    B0.y = fmaf(d0.y, c0.y, B0.y);
+                    A1.x = fmaf(s1.x, c1.x, A1.x);
+                    A1.y = fmaf(s1.y, c1.x, A1.y);
+                    B1.x = fmaf(d1.x, c1.y, B1.x);
+                    B1.y = fmaf(d1.y, c1.y, B1.y);
+                }
+                const int ob0 = (j0 / Ns) * Ns * r + j0 % Ns;
+                a[ob0 + qp0 * Ns] = make_float2(A0.x - sg * B0.y, A0.y + sg * B0.x);
+                a[ob0 + (r - qp0) * Ns] = make_float2(A0.x + sg * B0.y, A0.y - sg * B0.x);
+                if (has1) {
+                    const int ob1 = (j1 / Ns) * Ns * r + j1 % Ns;
+                    a[ob1 + qp1 * Ns] = make_float2(A1.x - sg * B1.y, A1.y + sg * B1.x);
+                    a[ob1 + (r - qp1) * Ns] = make_float2(A1.x + sg * B1.y, A1.y - sg * B1.x);
                 }
             }
             __syncwarp();
@@ -210,7 +228,7 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
     float2* sp1 = sp0 + M1;
 
     // z = a + i b from the two half-spectrum rows (Hermitian extension beyond M1)
-#pragma unroll 1
+#pragma unroll 3
     for (int k = lane; k < W; k += 32) {
         float2 z;
         if (k < M1) {
@@ -226,61 +244,71 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
     float2* u = warp_dft(bufa, bufb, T, g.prow, true, lane);
     float2* o = (u == bufa) ? bufb : bufa;
     const float sigma = g.sigma, tau = g.tau;
+    // each element is read and written by one lane only: the state arrays do not alias
+    const float* __restrict__ fld = g.field;
+    const unsigned char* __restrict__ msk = g.mask;
+    const float* __restrict__ wgt = g.weight;
+    float* __restrict__ chi = g.chi;
+    float* __restrict__ cbar = g.chibar;
+    float* __restrict__ pp = g.p;
+    float* __restrict__ qxp = g.qx;
+    float* __restrict__ qyp = g.qy;
     if (g.phase == 0) {
         // dual step at both rows (Sec. II.A): p and q from u = D chibar and chibar's differences
         const bool down1 = (i1 + 1 < H);
-#pragma unroll 1
+        const float inv_den = g.inv_den;
+#pragma unroll 3
         for (int n = lane; n < W; n += 32) {
             const float2 uv = u[n];
             const bool right = (n + 1 < W);
             const size_t a0 = r0 + n, a1 = r1 + n;
-            const float c0 = __ldcg(g.chibar + a0), c1 = __ldcg(g.chibar + a1);
-            const float c0r = right ? __ldcg(g.chibar + a0 + 1) : c0;
-            const float c1r = right ? __ldcg(g.chibar + a1 + 1) : c1;
-            const float c2 = down1 ? __ldcg(g.chibar + a1 + W) : c1;
-            const float m0 = (float)__ldg(g.mask + a0), m1 = (float)__ldg(g.mask + a1);
-            const float w0 = g.weight ? __ldg(g.weight + a0) : m0;
-            const float w1 = g.weight ? __ldg(g.weight + a1) : m1;
-            const float p0 = (__ldcg(g.p + a0) + sigma * (w0 * (uv.x - __ldg(g.field + a0)))) * g.inv_den;
-            const float p1 = (__ldcg(g.p + a1) + sigma * (w1 * (uv.y - __ldg(g.field + a1)))) * g.inv_den;
-            float qx0 = __ldcg(g.qx + a0) + sigma * m0 * (c0r - c0);
-            float qy0 = __ldcg(g.qy + a0) + sigma * m0 * (c1 - c0);
-            float qx1 = __ldcg(g.qx + a1) + sigma * m1 * (c1r - c1);
-            float qy1 = __ldcg(g.qy + a1) + sigma * m1 * (c2 - c1);
+            const float c0 = __ldcg(cbar + a0), c1 = __ldcg(cbar + a1);
+            const float c0r = right ? __ldcg(cbar + a0 + 1) : c0;
+            const float c1r = right ? __ldcg(cbar + a1 + 1) : c1;
+            const float c2 = down1 ? __ldcg(cbar + a1 + W) : c1;
+            const float m0 = (float)__ldg(msk + a0), m1 = (float)__ldg(msk + a1);
+            const float w0 = wgt ? __ldg(wgt + a0) : m0;
+            const float w1 = wgt ? __ldg(wgt + a1) : m1;
+            const float p0 = (__ldcg(pp + a0) + sigma * (w0 * (uv.x - __ldg(fld + a0)))) * inv_den;
+            const float p1 = (__ldcg(pp + a1) + sigma * (w1 * (uv.y - __ldg(fld + a1)))) * inv_den;
+            float qx0 = __ldcg(qxp + a0) + sigma * m0 * (c0r - c0);
+            float qy0 = __ldcg(qyp + a0) + sigma * m0 * (c1 - c0);
+            float qx1 = __ldcg(qxp + a1) + sigma * m1 * (c1r - c1);
+            float qy1 = __ldcg(qyp + a1) + sigma * m1 * (c2 - c1);
             tv_prox(qx0, qy0, g.tv_iso);
             tv_prox(qx1, qy1, g.tv_iso);
-            __stcg(g.p + a0, p0);
-            __stcg(g.p + a1, p1);
-            __stcg(g.qx + a0, qx0);
-            __stcg(g.qy + a0, qy0);
-            __stcg(g.qx + a1, qx1);
-            __stcg(g.qy + a1, qy1);
+            __stcg(pp + a0, p0);
+            __stcg(pp + a1, p1);
+            __stcg(qxp + a0, qx0);
+            __stcg(qyp + a0, qy0);
+            __stcg(qxp + a1, qx1);
+            __stcg(qyp + a1, qy1);
             o[n] = make_float2(w0 * p0, w1 * p1);  // W p, transformed next
         }
     } else {
         // primal step: chi+ = chi - tau (v + G^T q), v = D W p; chibar = 2 chi+ - chi.
         // q is zero wherever the 0/1 mask is (zero start, masked increments), so M q = q.
         const bool up0 = (i0 > 0), down1 = (i1 + 1 < H);
-#pragma unroll 1
+#pragma unroll 3
         for (int n = lane; n < W; n += 32) {
             const float2 vv = u[n];
             const size_t a0 = r0 + n, a1 = r1 + n;
-            const float qx0 = __ldcg(g.qx + a0), qx1 = __ldcg(g.qx + a1);
-            const float qy0 = __ldcg(g.qy + a0), qy1 = __ldcg(g.qy + a1);
-            const float qxl0 = (n > 0) ? __ldcg(g.qx + a0 - 1) : 0.f;
-            const float qxl1 = (n > 0) ? __ldcg(g.qx + a1 - 1) : 0.f;
-            const float qyu0 = up0 ? __ldcg(g.qy + a0 - W) : 0.f;
+            const float qx0 = __ldcg(qxp + a0), qx1 = __ldcg(qxp + a1);
+            const float qy0 = __ldcg(qyp + a0), qy1 = __ldcg(qyp + a1);
+            const float qxl0 = (n > 0) ? __ldcg(qxp + a0 - 1) : 0.f;
+            const float qxl1 = (n > 0) ? __ldcg(qxp + a1 - 1) : 0.f;
+            const float qyu0 = up0 ? __ldcg(qyp + a0 - W) : 0.f;
             const bool last_col = (n + 1 == W);
             const float d0 = (qxl0 - (last_col ? 0.f : qx0)) + (qyu0 - qy0);  // row i0 < H - 1
             const float d1 = (qxl1 - (last_col ? 0.f : qx1)) + (qy0 - (down1 ? qy1 : 0.f));
-            const float c0 = __ldcg(g.chi + a0), c1 = __ldcg(g.chi + a1);
+            const float c0 = __ldcg(chi + a0), c1 = __ldcg(chi + a1);
             const float n0 = c0 - tau * vv.x - tau * d0;
             const float n1 = c1 - tau * vv.y - tau * d1;
-            __stcg(g.chi + a0, n0);
-            __stcg(g.chi + a1, n1);
+            __stcg(chi + a0, n0);
+            __stcg(chi + a1, n1);
             const float b0 = 2.f * n0 - c0, b1 = 2.f * n1 - c1;
-            __stcg(g.chibar + a0, b0);
-            __stcg(g.chibar + a1, b1);
+            __stcg(cbar + a0, b0);
+            __stcg(cbar + a1, b1);
             o[n] = make_float2(b0, b1);
         }
     }
@@ -288,7 +316,7 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
     if (g.phase == 0 || g.store) {
         float2* Z = warp_dft(o, u, T, g.prow, false, lane);
         // split: A = (Z(k) + conj Z(-k)) / 2, B = (Z(k) - conj Z(-k)) / (2 i)
-#pragma unroll 1
+#pragma unroll 3
         for (int k = lane; k < M1; k += 32) {
             const float2 zk = Z[k], zm = Z[k == 0 ? 0 : W - k];
             __stcg(sp0 + k, make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y)));
