@@ -55,6 +55,20 @@ pcs_status failg(pcs_status st, const char* what, cudaError_t e = cudaSuccess) {
     return pcs::set_last_error(st, buf);
 }
 
+// Column pass: the register-FFT kernel for these H, else the shared-memory DFT kernel.
+struct ColEntry {
+    int H;
+    size_t smem;
+    void (*kern)(GenParams);
+    int tile;  // columns per CTA
+};
+template <int H>
+constexpr ColEntry col_entry() {
+    return ColEntry{H, pcs::GeoCol<H>::SMEM_BYTES, &pcs::gen_cols_fft_kernel<H>, pcs::GeoCol<H>::TY};
+}
+const ColEntry k_cols[] = {col_entry<64>(),  col_entry<128>(), col_entry<192>(),
+                           col_entry<256>(), col_entry<384>(), col_entry<512>()};
+
 size_t rows_smem(int W) { return sizeof(float2) * (size_t)W * (1 + 2 * pcs::kGenRowWarps); }
 size_t cols_smem(int H) { return sizeof(float2) * ((size_t)H + (size_t)(2 * H + 1) * pcs::kGenColTile); }
 
@@ -95,7 +109,13 @@ pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mas
     float2* tabs = nullptr;  // row twiddles, then column twiddles
     cudaError_t e;
     pcs_status ret = PCS_OK;
-    const size_t srows = rows_smem(W), scols = cols_smem(H);
+    const ColEntry* ce = nullptr;
+    for (const auto& c : k_cols)
+        if (c.H == H) ce = &c;
+    void (*cols_kern)(GenParams) = ce ? ce->kern : pcs::gen_cols_kernel;
+    const int col_tile = ce ? ce->tile : pcs::kGenColTile;
+    const int col_threads = ce ? 256 : pcs::kGenColTile * 32;
+    const size_t srows = rows_smem(W), scols = ce ? ce->smem : cols_smem(H);
     if ((e = cudaMalloc(&state, 4 * n * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&spec, nspec * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&tabs, (size_t)(W + H) * sizeof(float2))) != cudaSuccess) {
@@ -109,8 +129,8 @@ pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mas
                (e = cudaMemsetAsync(spec, 0, nspec * sizeof(float2), st)) != cudaSuccess ||
                (e = cudaFuncSetAttribute(pcs::gen_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)srows)) != cudaSuccess ||
-               (e = cudaFuncSetAttribute(pcs::gen_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)scols)) != cudaSuccess) {
+               (e = cudaFuncSetAttribute(cols_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scols)) !=
+                   cudaSuccess) {
         ret = failg(PCS_ECUDA, "set-up", e);
     } else {
         g.field = field;
@@ -135,18 +155,18 @@ pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mas
         g.b0_axis = b0_axis;
         const int pairs = S * (H / 2);
         const dim3 grid_r((pairs + pcs::kGenRowWarps - 1) / pcs::kGenRowWarps);
-        const dim3 grid_c((M1 + pcs::kGenColTile - 1) / pcs::kGenColTile, S);
+        const dim3 grid_c((M1 + col_tile - 1) / col_tile, S);
         // iteration n: dual step from the spectrum D F chibar_n (zero at n = 0), column pass
         // (spectrum of W p), primal step, column pass (spectrum of chibar_{n+1}; not after the last)
         for (int it = 0; it < n_iter; ++it) {
             g.phase = 0;
             g.store = 1;
             pcs::gen_rows_kernel<<<grid_r, pcs::kGenRowWarps * 32, srows, st>>>(g);
-            pcs::gen_cols_kernel<<<grid_c, pcs::kGenColTile * 32, scols, st>>>(g);
+            cols_kern<<<grid_c, col_threads, scols, st>>>(g);
             g.phase = 1;
             g.store = it + 1 < n_iter;
             pcs::gen_rows_kernel<<<grid_r, pcs::kGenRowWarps * 32, srows, st>>>(g);
-            if (g.store) pcs::gen_cols_kernel<<<grid_c, pcs::kGenColTile * 32, scols, st>>>(g);
+            if (g.store) cols_kern<<<grid_c, col_threads, scols, st>>>(g);
             if ((e = cudaGetLastError()) != cudaSuccess) {
                 ret = failg(PCS_ECUDA, "launch", e);
                 break;

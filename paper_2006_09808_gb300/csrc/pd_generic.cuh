@@ -56,6 +56,12 @@ __device__ __forceinline__ float2 gcmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// floor(j / d) for 0 <= j < 1024 and 1 <= d <= 512, from inv = 1/d rounded to float:
+// (j + 1/2) inv stays within 1e-4 of (j + 1/2)/d, which is at least 1/(2d) >= 1e-3 from
+// an integer (checked exhaustively over that range).  Replaces integer division by
+// the runtime stage sizes.
+__device__ __forceinline__ int qdiv(int j, float inv) { return (int)(((float)j + 0.5f) * inv); }
+
 // Length pl.n DFT by one warp in shared memory (unnormalised; inv: exponent sign +).
 // Input in a, b is scratch; returns the buffer holding the result (which one depends
 // on the plan's radices).  Stage with
@@ -71,21 +77,22 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
         const int r = pl.r[st];
         const int R = N / r;
         const int step = N / (Ns * r);
+        const float invNs = __frcp_rn((float)Ns), invR = __frcp_rn((float)R);
         if (r == 2) {
 #pragma unroll 1
             for (int j = lane; j < R; j += 32) {
-                const int k = j % Ns;
+                const int k = j - qdiv(j, invNs) * Ns;
                 float2 t = T[k * step];
                 t.y *= sg;
                 const float2 v0 = a[j], v1 = gcmul(a[j + R], t);
-                const int o = (j / Ns) * Ns * 2 + k;
+                const int o = (j - k) * 2 + k;
                 b[o] = make_float2(v0.x + v1.x, v0.y + v1.y);
                 b[o + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
             }
         } else if (r == 4) {
 #pragma unroll 1
             for (int j = lane; j < R; j += 32) {
-                const int k = j % Ns;
+                const int k = j - qdiv(j, invNs) * Ns;
                 float2 t1 = T[k * step], t2 = T[2 * k * step], t3 = T[3 * k * step];
                 t1.y *= sg;
                 t2.y *= sg;
@@ -96,7 +103,7 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
                 const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y), d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
                 // -i d13 (forward) or +i d13 (inverse)
                 const float2 rd = make_float2(sg * d13.y, -sg * d13.x);
-                const int o = (j / Ns) * Ns * 4 + k;
+                const int o = (j - k) * 4 + k;
                 b[o] = make_float2(s02.x + s13.x, s02.y + s13.y);
                 b[o + Ns] = make_float2(d02.x + rd.x, d02.y + rd.y);
                 b[o + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
@@ -106,7 +113,7 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
             const float h = 0.86602540378443865f;  // sin(2 pi / 3)
 #pragma unroll 1
             for (int j = lane; j < R; j += 32) {
-                const int k = j % Ns;
+                const int k = j - qdiv(j, invNs) * Ns;
                 float2 t1 = T[k * step], t2 = T[2 * k * step];
                 t1.y *= sg;
                 t2.y *= sg;
@@ -115,7 +122,7 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
                 const float2 m = make_float2(v0.x - 0.5f * s.x, v0.y - 0.5f * s.y);
                 // -i h d (forward) or +i h d (inverse)
                 const float2 rd = make_float2(sg * h * d.y, -sg * h * d.x);
-                const int o = (j / Ns) * Ns * 3 + k;
+                const int o = (j - k) * 3 + k;
                 b[o] = make_float2(v0.x + s.x, v0.y + s.y);
                 b[o + Ns] = make_float2(m.x + rd.x, m.y + rd.y);
                 b[o + 2 * Ns] = make_float2(m.x - rd.x, m.y - rd.y);
@@ -127,8 +134,8 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
             // X_q' = A + i sg B, X_(r-q') = A - i sg B (forward sg = 1).  The result lands in a.
 #pragma unroll 1
             for (int u = lane + R; u < N; u += 32) {
-                const int j = u % R, q = u / R;
-                float2 t = T[(j % Ns) * step * q];
+                const int q = qdiv(u, invR), j = u - q * R;
+                float2 t = T[(j - qdiv(j, invNs) * Ns) * step * q];
                 t.y *= sg;
                 a[u] = gcmul(a[u], t);
             }
@@ -136,7 +143,7 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
             const int h = (r - 1) / 2;
 #pragma unroll 1
             for (int u = lane; u < R * (h + 1); u += 32) {
-                const int j = u % R, q = u / R;
+                const int q = qdiv(u, invR), j = u - q * R;
                 if (q == 0) {
                     b[j] = a[j];
                 } else {
@@ -156,7 +163,8 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
                     acc.x += sq.x;
                     acc.y += sq.y;
                 }
-                a[(j / Ns) * Ns * r + j % Ns] = acc;
+                const int k = j - qdiv(j, invNs) * Ns;
+                a[(j - k) * r + k] = acc;
             }
             // q' = 1..h: two (j, q') units per lane at a time (independent chains)
             const int NU = R * h;
@@ -164,8 +172,9 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
             for (int u0 = lane; u0 < NU; u0 += 64) {
                 const bool has1 = (u0 + 32 < NU);
                 const int u1 = has1 ? u0 + 32 : u0;
-                const int j0 = u0 % R, qp0 = 1 + u0 / R;
-                const int j1 = u1 % R, qp1 = 1 + u1 / R;
+                const int t0 = qdiv(u0, invR), t1 = qdiv(u1, invR);
+                const int j0 = u0 - t0 * R, qp0 = 1 + t0;
+                const int j1 = u1 - t1 * R, qp1 = 1 + t1;
                 float2 A0 = b[j0], B0 = make_float2(0.f, 0.f);
                 float2 A1 = b[j1], B1 = make_float2(0.f, 0.f);
                 int m0 = 0, m1 = 0;
@@ -187,11 +196,13 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
                     B1.x = fmaf(d1.x, c1.y, B1.x);
                     B1.y = fmaf(d1.y, c1.y, B1.y);
                 }
-                const int ob0 = (j0 / Ns) * Ns * r + j0 % Ns;
+                const int k0 = j0 - qdiv(j0, invNs) * Ns;
+                const int ob0 = (j0 - k0) * r + k0;
                 a[ob0 + qp0 * Ns] = make_float2(A0.x - sg * B0.y, A0.y + sg * B0.x);
                 a[ob0 + (r - qp0) * Ns] = make_float2(A0.x + sg * B0.y, A0.y - sg * B0.x);
                 if (has1) {
-                    const int ob1 = (j1 / Ns) * Ns * r + j1 % Ns;
+                    const int k1 = j1 - qdiv(j1, invNs) * Ns;
+                    const int ob1 = (j1 - k1) * r + k1;
                     a[ob1 + qp1 * Ns] = make_float2(A1.x - sg * B1.y, A1.y + sg * B1.x);
                     a[ob1 + (r - qp1) * Ns] = make_float2(A1.x + sg * B1.y, A1.y - sg * B1.x);
                 }
@@ -375,6 +386,60 @@ __global__ void __launch_bounds__(kGenColTile * 32) gen_cols_kernel(GenParams g)
         float2* dst = spec + kx0 + c;
 #pragma unroll 4
         for (int ky = ky0; ky < H; ky += KY_STEP) __stcg(dst + (size_t)ky * M1, cols[(size_t)c * CS + ky]);
+    }
+}
+
+// Column pass for H with a compiled register FFT (64·2^k, 3·2^k up to 512):
+// pencils of TZ = H / EZ lanes, one per spectrum column; a CTA takes TY adjacent
+// columns of one slice, so lanes of adjacent pencils read adjacent addresses.
+template <int H>
+struct GeoCol {
+    static constexpr int EZ = default_elems(H);
+    static constexpr int TZ = H / EZ;
+    static constexpr int PPW = 32 / TZ;         // pencils per warp
+    static constexpr int NT = 256;
+    static constexpr int TY = (NT / 32) * PPW;  // columns per CTA
+    static constexpr int NP = H + (TZ % 16);    // pencil buffer stride
+    static constexpr size_t SMEM_BYTES = sizeof(float2) * (TY * NP + StageTw<H, EZ>::SIZE);
+};
+
+template <int H>
+__global__ void __launch_bounds__(256) gen_cols_fft_kernel(GenParams g) {
+    using GC = GeoCol<H>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TZ = GC::TZ, EZ = GC::EZ;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + GC::TY * GC::NP;
+    StageTw<H, EZ>::fill(stw, g.tcol, 1, threadIdx.x, GC::NT);
+    __syncthreads();
+    const int W = g.W, M1 = g.M1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gi = lane % TZ;
+    const int pen = warp * GC::PPW + lane / TZ;
+    const unsigned gm = group_mask<TZ>(lane);
+    const int kx_raw = blockIdx.x * GC::TY + pen;
+    const bool live = kx_raw < M1;
+    const int kx = live ? kx_raw : M1 - 1;  // idle pencils repeat the last column, store nothing
+    float2* col = g.spec + (size_t)blockIdx.y * H * M1 + kx;
+    float2* pb = buf + pen * GC::NP;
+    float2 x[EZ];
+#pragma unroll
+    for (int e = 0; e < EZ; ++e) x[e] = __ldcg(col + (size_t)(gi + TZ * e) * M1);
+    fft<H, TZ, false>(x, pb, stw, gi, gm);
+    const float fx = (float)kx / (float)W;
+    const float scale = 1.0f / ((float)H * (float)W);
+#pragma unroll
+    for (int e = 0; e < EZ; ++e) {
+        const float fy = gen_freq(gi + TZ * e, H);
+        const float k2 = fx * fx + fy * fy;
+        const float fb = g.b0_axis ? fx : fy;
+        const float d = (k2 > 0.f) ? (1.0f / 3.0f - (fb * fb) / k2) * scale : 0.f;
+        x[e] = make_float2(x[e].x * d, x[e].y * d);
+    }
+    fft<H, TZ, true>(x, pb, stw, gi, gm);
+    if (live) {
+#pragma unroll
+        for (int e = 0; e < EZ; ++e) __stcg(col + (size_t)(gi + TZ * e) * M1, x[e]);
     }
 }
 

@@ -1,7 +1,8 @@
 """Any-size per-slice solver (pcs_solve_slices_generic) against the FP64 oracle.
 
 Sizes include the paper's own slices, 256 x 258 and 128 x 132 (FFT lengths with the
-prime factors 43 and 11), rectangles, and the smallest accepted size.  tau = sigma =
+prime factors 43 and 11), rectangles, and the smallest accepted size; H in {64·2^k, 3·2^k}
+takes the register-FFT column kernel, other H the shared-memory DFT column kernel.  tau = sigma =
 1/sqrt(4/9 + 8), a valid step for every 0/1 mask (||D|| <= 2/3, ||G||^2 <= 8).
 """
 
@@ -38,9 +39,9 @@ def rel_l2(a, b):
 
 
 def gpu_generic(field, mask, lam, n_iter, tv=0, weight=None, b0_axis=0):
-    f = torch.from_numpy(np.ascontiguousarray(field, dtype=np.float32)).cuda()
-    m = torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint8)).cuda()
-    w = None if weight is None else torch.from_numpy(np.ascontiguousarray(weight, dtype=np.float32)).cuda()
+    f = torch.from_numpy(np.array(field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.array(mask, dtype=np.uint8)).cuda()
+    w = None if weight is None else torch.from_numpy(np.array(weight, dtype=np.float32)).cuda()
     chi = torch.full_like(f, float("nan"))
     pcs.pcs_solve_slices_generic(f, m, lam, STEP, STEP, n_iter, chi, tv=tv, weight=w, b0_axis=b0_axis)
     torch.cuda.synchronize()
@@ -63,6 +64,9 @@ def oracle(field, mask, lam, n_iter, tv=0, weight=None, b0_axis=0):
         (2, 90, 98, 80, 1.0, 0, 0),     # 2·3²·5 x 2·7²
         (5, 30, 42, 150, 1.0, 1, 1),
         (2, 64, 64, 80, 1.0, 0, 0),     # power of two: the same problem as the compiled variants
+        (2, 192, 198, 60, 1.0, 0, 0),   # register-FFT column pass at H = 3·2^6; 198 = 2·3²·11
+        (1, 512, 46, 60, 1.0, 1, 0),    # H = 512, W = 2·23
+        (1, 384, 130, 40, 1.0, 0, 1),   # H = 3·2^7, W = 2·5·13
     ],
 )
 def test_parity_generic(S, H, W, n_iter, lam, tv, b0):
