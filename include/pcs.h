@@ -104,6 +104,14 @@ PCS_API int pcs_supported_size(int H, int W);
  *   opt         NULL for defaults
  *   cuda_stream a cudaStream_t (NULL = legacy default stream) used by every
  *               later call on this context
+ * Sizes without a compiled kernel (pcs_supported_size = 0) that
+ * pcs_supported_generic accepts, such as 256 x 258, make an any-size context
+ * when opt leaves cluster_size, kernel and threads at 0: pcs_solve_slices,
+ * pcs_solve_slices_weighted and pcs_solve_slices_host then run the row and
+ * column kernels of pcs_solve_slices_generic on the context's scratch and
+ * stream (asynchronous, no allocation; use_graph has no effect), while FP64
+ * reports (rep), pcs_report, pcs_opnorm and monitored solves return
+ * PCS_EUNSUPPORTED.
  * Errors: PCS_EINVAL (out NULL, max_slices < 1), PCS_EUNSUPPORTED (size),
  *         PCS_ECUDA (no device), PCS_ENOMEM.
  */

@@ -129,12 +129,24 @@ void build_twiddles(int n, std::vector<float2>& tw) { build_twiddles_t<float2>(n
 
 // ------------------------------------------------------------------ context
 
+namespace pcs {
+// any-size slices (pd_generic.cu)
+struct GenSolver;
+bool gen_supported(int H, int W);
+cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axis, int tv);
+void gen_destroy(GenSolver* gs);
+cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
+                        float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
+                        double sigma, int n_iter, cudaStream_t st);
+}  // namespace pcs
+
 struct pcs_ctx {
     int H = 0, W = 0, max_slices = 0;
     pcs_options opt{};
     cudaStream_t stream = nullptr;
     int device = 0;
-    const pcs::KernelEntry* entry = nullptr;
+    const pcs::KernelEntry* entry = nullptr;  // NULL for an any-size context
+    pcs::GenSolver* gen = nullptr;            // any-size context: row/column kernels (pd_generic.cu)
     int max_clusters = 0;
     int max_clusters_aux = 0;
     int last_iters = 0;
@@ -183,6 +195,7 @@ void free_ctx(pcs_ctx* c) {
         if (q) cudaFree(q);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
+    pcs::gen_destroy(c->gen);
     delete c;
 }
 
@@ -241,6 +254,16 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
                         const float* weight = nullptr) {
     if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out) || !aligned16(weight))
         return fail(PCS_EINVAL, "device buffers must be 16-byte aligned");
+    if (ctx->gen) {
+        if (inv_den_slice || entry || resume || active)
+            return fail(PCS_EUNSUPPORTED, "per-slice lambdas, resumed and monitored solves need a compiled size");
+        PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+        PCS_CUDA(pcs::gen_enqueue(ctx->gen, field, mask, weight, chi_out, ctx->chibar, ctx->p, ctx->qx, ctx->qy, S,
+                                  lambda, tau, sigma, n_iter, ctx->stream),
+                 "launch of the any-size kernels");
+        ctx->last_iters = n_iter;
+        return PCS_OK;
+    }
     pcs::PDParams prm;
     std::memset(&prm, 0, sizeof(prm));  // padding too: the graph cache compares whole structs
     prm.field = field;
@@ -393,6 +416,7 @@ namespace pcs {
 // (chi, p, q) where p, q are the context's dual state of the last solve.
 pcs_status ctx_report(pcs_ctx* c, const float* field, const unsigned char* mask, int S, double lambda,
                       const float* chi, pcs_slice_report* rep, const float* weight) {
+    if (c->gen) return fail(PCS_EUNSUPPORTED, "FP64 diagnostics need a compiled slice size");
     pcs_status st = ensure_aux(c);
     if (st != PCS_OK) return st;
     AuxParams a = aux_params(c, S);
@@ -424,6 +448,7 @@ pcs_status ctx_report(pcs_ctx* c, const float* field, const unsigned char* mask,
 }
 
 pcs_status ctx_opnorm(pcs_ctx* c, const unsigned char* mask, int S, int power_iters, double* L_out) {
+    if (c->gen) return fail(PCS_EUNSUPPORTED, "the power iteration needs a compiled slice size");
     pcs_status st = ensure_aux(c);
     if (st != PCS_OK) return st;
     AuxParams a = aux_params(c, S);
@@ -462,7 +487,9 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
     if (o.use_graph && cuda_stream == nullptr)
         return fail(PCS_EINVAL, "use_graph needs a non-NULL stream (the legacy stream cannot be captured)");
     const pcs::KernelEntry* entry = find_entry(H, W, o.cluster_size, o.kernel, o.threads);
-    if (!entry)
+    const bool any_size = !entry && find_entry(H, W, 0) == nullptr && o.cluster_size == 0 && o.kernel == 0 &&
+                          o.threads == 0 && pcs::gen_supported(H, W);
+    if (!entry && !any_size)
         return fail(PCS_EUNSUPPORTED, "no kernel for %d x %d slices with cluster_size %d, kernel %d, threads %d", H,
                     W, o.cluster_size, o.kernel, o.threads);
 
@@ -482,6 +509,19 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
         return st;
     };
     if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+    if (any_size) {
+        // the any-size row/column kernels: their own tables and spectrum; the state as below
+        const size_t n = slice_elems(c) * (size_t)max_slices;
+        if ((e = pcs::gen_create(&c->gen, H, W, max_slices, o.b0_axis, o.tv)) != cudaSuccess)
+            return bail(cuda_fail(e, "any-size set-up"));
+        float** st[] = {&c->chibar, &c->p, &c->qx, &c->qy};
+        for (float** q : st)
+            if ((e = cudaMalloc(q, n * sizeof(float))) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+        if ((e = cudaMalloc(&c->err, sizeof(int))) != cudaSuccess || (e = cudaMemset(c->err, 0, sizeof(int))) != cudaSuccess)
+            return bail(cuda_fail(e, "cudaMalloc"));
+        *out = c;
+        return PCS_OK;
+    }
     if ((e = entry->prepare(&c->max_clusters, &c->max_clusters_aux)) != cudaSuccess) return bail(cuda_fail(e, "kernel attributes"));
     if (c->max_clusters < 1)
         return bail(fail(PCS_ECUDA, "kernel %dx%d/C=%d cannot be made resident", H, W, entry->C));
@@ -572,6 +612,7 @@ pcs_status pcs_solve_slices(pcs_ctx* ctx, const float* field, const unsigned cha
                             double tau, double sigma, int n_iter, float* chi_out, pcs_slice_report* rep) {
     pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || S == 0) return st;
+    if (rep && ctx->gen) return fail(PCS_EUNSUPPORTED, "FP64 diagnostics need a compiled slice size");
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
     st = launch_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
@@ -585,7 +626,8 @@ pcs_status pcs_solve_slices_weighted(pcs_ctx* ctx, const float* field, const uns
     pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || S == 0) return st;
     if (!weight) return fail(PCS_EINVAL, "weight is NULL");
-    if (ctx->entry->resident)
+    if (rep && ctx->gen) return fail(PCS_EUNSUPPORTED, "FP64 diagnostics need a compiled slice size");
+    if (ctx->entry && ctx->entry->resident)
         return fail(PCS_EUNSUPPORTED, "weighted solves run on the streaming kernel (create the context with kernel 1)");
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
@@ -600,6 +642,7 @@ pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const un
                                  pcs_slice_report* rep) {
     pcs_status st = validate_solve(ctx, field_host, mask_host, S, lambda, tau, sigma, n_iter, chi_out_host);
     if (st != PCS_OK || S == 0) return st;
+    if (rep && ctx->gen) return fail(PCS_EUNSUPPORTED, "FP64 diagnostics need a compiled slice size");
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -649,6 +692,7 @@ pcs_status pcs_solve_slices_monitored(pcs_ctx* ctx, const float* field, const un
     if (!rep) return fail(PCS_EINVAL, "rep is required");
     if (check_every < 1) return fail(PCS_EINVAL, "check_every must be >= 1");
     if (!(rel_gap_tol >= 0.0)) return fail(PCS_EINVAL, "rel_gap_tol must be >= 0");
+    if (ctx->gen) return fail(PCS_EUNSUPPORTED, "monitored solves need a compiled slice size");
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");

@@ -72,14 +72,136 @@ const ColEntry k_cols[] = {col_entry<64>(),  col_entry<128>(), col_entry<192>(),
 size_t rows_smem(int W) { return sizeof(float2) * (size_t)W * (1 + 2 * pcs::kGenRowWarps); }
 size_t cols_smem(int H) { return sizeof(float2) * ((size_t)H + (size_t)(2 * H + 1) * pcs::kGenColTile); }
 
+bool gen_shape_ok(int H, int W, GenPlan* prow, GenPlan* pcol) {
+    return H % 2 == 0 && W % 2 == 0 && gen_plan(W, prow) && gen_plan(H, pcol);
+}
+
 }  // namespace
+
+namespace pcs {
+
+// Tables, plans, kernel choice and the half-spectrum scratch of one H x W size.
+struct GenSolver {
+    GenParams g;  // plans, sizes, tables and spectrum set; state pointers per solve
+    float2* tabs = nullptr;
+    float2* spec = nullptr;
+    int max_slices = 0;
+    void (*cols_kern)(GenParams) = nullptr;
+    int col_tile = 0, col_threads = 0;
+    size_t srows = 0, scols = 0;
+};
+
+bool gen_supported(int H, int W) {
+    GenPlan a, b;
+    return gen_shape_ok(H, W, &a, &b);
+}
+
+void gen_destroy(GenSolver* gs) {
+    if (!gs) return;
+    cudaFree(gs->tabs);
+    cudaFree(gs->spec);
+    delete gs;
+}
+
+// Returns cudaSuccess and *out, or an error with *out = NULL.  The twiddle tables are
+// uploaded synchronously.
+cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axis, int tv) {
+    *out = nullptr;
+    GenSolver* gs = new GenSolver();
+    std::memset(&gs->g, 0, sizeof(gs->g));
+    if (!gen_shape_ok(H, W, &gs->g.prow, &gs->g.pcol)) {
+        delete gs;
+        return cudaErrorInvalidValue;
+    }
+    const int M1 = W / 2 + 1;
+    const ColEntry* ce = nullptr;
+    for (const auto& c : k_cols)
+        if (c.H == H) ce = &c;
+    gs->cols_kern = ce ? ce->kern : gen_cols_kernel;
+    gs->col_tile = ce ? ce->tile : kGenColTile;
+    gs->col_threads = ce ? 256 : kGenColTile * 32;
+    gs->srows = rows_smem(W);
+    gs->scols = ce ? ce->smem : cols_smem(H);
+    gs->max_slices = max_slices;
+    std::vector<float2> tw_r, tw_c;
+    build_twiddles(W, tw_r);
+    build_twiddles(H, tw_c);
+    cudaError_t e;
+    if ((e = cudaMalloc(&gs->tabs, (size_t)(W + H) * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&gs->spec, (size_t)max_slices * H * M1 * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMemcpy(gs->tabs, tw_r.data(), W * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(gs->tabs + W, tw_c.data(), H * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(gen_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->srows)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(gs->cols_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->scols)) !=
+            cudaSuccess) {
+        gen_destroy(gs);
+        return e;
+    }
+    GenParams& g = gs->g;
+    g.spec = gs->spec;
+    g.trow = gs->tabs;
+    g.tcol = gs->tabs + W;
+    g.H = H;
+    g.W = W;
+    g.M1 = M1;
+    g.tv_iso = tv;
+    g.b0_axis = b0_axis;
+    *out = gs;
+    return cudaSuccess;
+}
+
+// Enqueue a solve of S <= max_slices slices on st: zero state, chi and spectrum, then
+// n_iter iterations of four launches.  Asynchronous; no allocation.
+cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
+                        float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
+                        double sigma, int n_iter, cudaStream_t st) {
+    GenParams g = gs->g;
+    const size_t n = (size_t)S * g.H * g.W;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(chibar, 0, n * sizeof(float), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p, 0, n * sizeof(float), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(qx, 0, n * sizeof(float), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(qy, 0, n * sizeof(float), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(chi, 0, n * sizeof(float), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(g.spec, 0, (size_t)S * g.H * g.M1 * sizeof(float2), st)) != cudaSuccess)
+        return e;
+    g.field = field;
+    g.mask = mask;
+    g.weight = weight;
+    g.chi = chi;
+    g.chibar = chibar;
+    g.p = p;
+    g.qx = qx;
+    g.qy = qy;
+    g.S = S;
+    g.sigma = (float)sigma;
+    g.tau = (float)tau;
+    g.inv_den = (float)(1.0 / (1.0 + sigma / lambda));
+    const int pairs = S * (g.H / 2);
+    const dim3 grid_r((pairs + kGenRowWarps - 1) / kGenRowWarps);
+    const dim3 grid_c((g.M1 + gs->col_tile - 1) / gs->col_tile, S);
+    // iteration n: dual step from the spectrum D F chibar_n (zero at n = 0), column pass
+    // (spectrum of W p), primal step, column pass (spectrum of chibar_{n+1}; not after the last)
+    for (int it = 0; it < n_iter; ++it) {
+        g.phase = 0;
+        g.store = 1;
+        gen_rows_kernel<<<grid_r, kGenRowWarps * 32, gs->srows, st>>>(g);
+        gs->cols_kern<<<grid_c, gs->col_threads, gs->scols, st>>>(g);
+        g.phase = 1;
+        g.store = it + 1 < n_iter;
+        gen_rows_kernel<<<grid_r, kGenRowWarps * 32, gs->srows, st>>>(g);
+        if (g.store) gs->cols_kern<<<grid_c, gs->col_threads, gs->scols, st>>>(g);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace pcs
 
 extern "C" {
 
-int pcs_supported_generic(int H, int W) {
-    GenPlan a, b;
-    return (H % 2 == 0 && W % 2 == 0 && gen_plan(H, &a) && gen_plan(W, &b)) ? 1 : 0;
-}
+int pcs_supported_generic(int H, int W) { return pcs::gen_supported(H, W) ? 1 : 0; }
 
 pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mask, const float* weight, int S,
                                     int H, int W, int b0_axis, double lambda, double tau, double sigma, int n_iter,
@@ -89,96 +211,29 @@ pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mas
     if (n_iter < 0) return failg(PCS_EINVAL, "n_iter must be >= 0");
     if (tv != 0 && tv != 1) return failg(PCS_EINVAL, "tv must be 0 or 1");
     if (b0_axis != 0 && b0_axis != 1) return failg(PCS_EINVAL, "b0_axis must be 0 or 1");
-    GenParams g;
-    std::memset(&g, 0, sizeof(g));
-    if (H % 2 != 0 || W % 2 != 0 || !gen_plan(W, &g.prow) || !gen_plan(H, &g.pcol))
+    if (!pcs::gen_supported(H, W))
         return failg(PCS_EUNSUPPORTED, "H and W must be even, in [8, 512], with prime factors <= 61");
     if (S == 0) return PCS_OK;
     if (!field || !mask || !chi_out) return failg(PCS_EINVAL, "NULL argument");
     if (field == chi_out) return failg(PCS_EINVAL, "chi_out must not alias field");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t n = (size_t)S * H * W;
-    const int M1 = W / 2 + 1;
-    const size_t nspec = (size_t)S * H * M1;
-    std::vector<float2> tw_r, tw_c;
-    pcs::build_twiddles(W, tw_r);
-    pcs::build_twiddles(H, tw_c);
-
+    pcs::GenSolver* gs = nullptr;
     float* state = nullptr;  // chibar, p, qx, qy
-    float2* spec = nullptr;
-    float2* tabs = nullptr;  // row twiddles, then column twiddles
-    cudaError_t e;
     pcs_status ret = PCS_OK;
-    const ColEntry* ce = nullptr;
-    for (const auto& c : k_cols)
-        if (c.H == H) ce = &c;
-    void (*cols_kern)(GenParams) = ce ? ce->kern : pcs::gen_cols_kernel;
-    const int col_tile = ce ? ce->tile : pcs::kGenColTile;
-    const int col_threads = ce ? 256 : pcs::kGenColTile * 32;
-    const size_t srows = rows_smem(W), scols = ce ? ce->smem : cols_smem(H);
-    if ((e = cudaMalloc(&state, 4 * n * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&spec, nspec * sizeof(float2))) != cudaSuccess ||
-        (e = cudaMalloc(&tabs, (size_t)(W + H) * sizeof(float2))) != cudaSuccess) {
-        ret = failg(PCS_ECUDA, "cudaMalloc", e);
-    } else if ((e = cudaMemcpyAsync(tabs, tw_r.data(), W * sizeof(float2), cudaMemcpyHostToDevice, st)) !=
-                   cudaSuccess ||
-               (e = cudaMemcpyAsync(tabs + W, tw_c.data(), H * sizeof(float2), cudaMemcpyHostToDevice, st)) !=
-                   cudaSuccess ||
-               (e = cudaMemsetAsync(state, 0, 4 * n * sizeof(float), st)) != cudaSuccess ||
-               (e = cudaMemsetAsync(chi_out, 0, n * sizeof(float), st)) != cudaSuccess ||
-               (e = cudaMemsetAsync(spec, 0, nspec * sizeof(float2), st)) != cudaSuccess ||
-               (e = cudaFuncSetAttribute(pcs::gen_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)srows)) != cudaSuccess ||
-               (e = cudaFuncSetAttribute(cols_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scols)) !=
-                   cudaSuccess) {
+    cudaError_t e;
+    if ((e = pcs::gen_create(&gs, H, W, S, b0_axis, tv)) != cudaSuccess ||
+        (e = cudaMalloc(&state, 4 * n * sizeof(float))) != cudaSuccess) {
         ret = failg(PCS_ECUDA, "set-up", e);
-    } else {
-        g.field = field;
-        g.mask = mask;
-        g.weight = weight;
-        g.chi = chi_out;
-        g.chibar = state;
-        g.p = state + n;
-        g.qx = state + 2 * n;
-        g.qy = state + 3 * n;
-        g.spec = spec;
-        g.trow = tabs;
-        g.tcol = tabs + W;
-        g.S = S;
-        g.H = H;
-        g.W = W;
-        g.M1 = M1;
-        g.sigma = (float)sigma;
-        g.tau = (float)tau;
-        g.inv_den = (float)(1.0 / (1.0 + sigma / lambda));
-        g.tv_iso = tv;
-        g.b0_axis = b0_axis;
-        const int pairs = S * (H / 2);
-        const dim3 grid_r((pairs + pcs::kGenRowWarps - 1) / pcs::kGenRowWarps);
-        const dim3 grid_c((M1 + col_tile - 1) / col_tile, S);
-        // iteration n: dual step from the spectrum D F chibar_n (zero at n = 0), column pass
-        // (spectrum of W p), primal step, column pass (spectrum of chibar_{n+1}; not after the last)
-        for (int it = 0; it < n_iter; ++it) {
-            g.phase = 0;
-            g.store = 1;
-            pcs::gen_rows_kernel<<<grid_r, pcs::kGenRowWarps * 32, srows, st>>>(g);
-            cols_kern<<<grid_c, col_threads, scols, st>>>(g);
-            g.phase = 1;
-            g.store = it + 1 < n_iter;
-            pcs::gen_rows_kernel<<<grid_r, pcs::kGenRowWarps * 32, srows, st>>>(g);
-            if (g.store) cols_kern<<<grid_c, col_threads, scols, st>>>(g);
-            if ((e = cudaGetLastError()) != cudaSuccess) {
-                ret = failg(PCS_ECUDA, "launch", e);
-                break;
-            }
-        }
+    } else if ((e = pcs::gen_enqueue(gs, field, mask, weight, chi_out, state, state + n, state + 2 * n, state + 3 * n,
+                                     S, lambda, tau, sigma, n_iter, st)) != cudaSuccess) {
+        ret = failg(PCS_ECUDA, "launch", e);
     }
     // synchronous: the call owns its scratch
     cudaError_t se = cudaStreamSynchronize(st);
     if (ret == PCS_OK && se != cudaSuccess) ret = failg(PCS_ECUDA, "stream sync", se);
     cudaFree(state);
-    cudaFree(spec);
-    cudaFree(tabs);
+    pcs::gen_destroy(gs);
     return ret;
 }
 

@@ -55,8 +55,9 @@ def test_host_side_argument_checks(lib):
     assert lib.pcs_create(None, 64, 64, 1, None, None) == pcs.PCS_EINVAL
     assert lib.pcs_create(ctypes.byref(h), 64, 64, 0, None, None) == pcs.PCS_EINVAL
     assert h.value is None
-    assert lib.pcs_create(ctypes.byref(h), 100, 100, 4, None, None) == pcs.PCS_EUNSUPPORTED
-    assert "100 x 100" in pcs.last_error()
+    # 100 x 134: no compiled kernel, and 134 = 2 x 67 is outside the any-size rule (primes <= 61)
+    assert lib.pcs_create(ctypes.byref(h), 100, 134, 4, None, None) == pcs.PCS_EUNSUPPORTED
+    assert "100 x 134" in pcs.last_error()
     bad = pcs.pcs_options()
     bad.b0_axis = 3
     assert lib.pcs_create(ctypes.byref(h), 64, 64, 4, ctypes.byref(bad), None) == pcs.PCS_EINVAL

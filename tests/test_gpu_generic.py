@@ -145,3 +145,38 @@ def test_generic_edge_cases_and_errors():
             pcs.pcs_solve_slices_generic(g, mk, args["lam"], STEP, STEP, 5, torch.empty_like(g), tv=args["tv"],
                                          b0_axis=args["b0_axis"])
         assert ei.value.status == pcs.PCS_EINVAL
+
+
+def test_any_size_context():
+    """pcs_create for a size without a compiled kernel makes an any-size context: the same
+    results as pcs_solve_slices_generic, bit for bit, with the context's scratch and stream;
+    repeated solves reuse it; diagnostics are refused before anything is launched."""
+    pb = phantoms.volume(128, 132, 5, seed=75, lam=1.0, n_iter=40)
+    direct = gpu_generic(pb.field, pb.mask, 1.0, 40, tv=1)
+    f = torch.from_numpy(np.array(pb.field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.array(pb.mask, dtype=np.uint8)).cuda()
+    stream = torch.cuda.Stream()
+    assert not pcs.pcs_supported_size(128, 132)
+    ctx = pcs.pcs_create(128, 132, 8, tv=1, stream=stream)
+    try:
+        for S in (5, 3):  # fewer slices than the capacity, then again on the same scratch
+            chi = torch.full_like(f[:S], float("nan"))
+            with torch.cuda.stream(stream):
+                pcs.pcs_solve_slices(ctx, f[:S].contiguous(), m[:S].contiguous(), 1.0, STEP, STEP, 40, chi)
+            stream.synchronize()
+            assert np.array_equal(chi.cpu().numpy(), direct[:S])
+        w = torch.from_numpy(np.array(phantoms.magnitude_weight(pb.mask, seed=76), dtype=np.float32)).cuda()
+        chi = torch.empty_like(f)
+        torch.cuda.synchronize()  # inputs made on the current stream; the context runs on its own
+        pcs.pcs_solve_slices_weighted(ctx, f, m, w, 1.0, STEP, STEP, 40, chi)
+        stream.synchronize()
+        assert rel_l2(chi.cpu().numpy(), oracle(pb.field, pb.mask, 1.0, 40, tv=1, weight=w.cpu().numpy())) <= TOL
+        with pytest.raises(pcs.PcsError) as ei:
+            pcs.pcs_solve_slices(ctx, f, m, 1.0, STEP, STEP, 40, chi, report=True)
+        assert ei.value.status == pcs.PCS_EUNSUPPORTED
+        pcs.pcs_check(ctx)
+    finally:
+        pcs.pcs_destroy(ctx)
+    with pytest.raises(pcs.PcsError) as ei:  # a compiled-kernel option cannot apply
+        pcs.pcs_create(128, 132, 8, cluster_size=2)
+    assert ei.value.status == pcs.PCS_EUNSUPPORTED

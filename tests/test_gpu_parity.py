@@ -286,8 +286,8 @@ def test_error_codes_on_gpu():
         assert ei.value.status == pcs.PCS_EINVAL
     finally:
         pcs.pcs_destroy(ctx)
-    with pytest.raises(pcs.PcsError) as ei:
-        pcs.pcs_create(96, 100, 1)
+    with pytest.raises(pcs.PcsError) as ei:  # no compiled kernel, and 134 = 2 x 67 outside the any-size rule
+        pcs.pcs_create(96, 134, 1)
     assert ei.value.status == pcs.PCS_EUNSUPPORTED
 
 
