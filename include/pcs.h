@@ -109,9 +109,9 @@ PCS_API int pcs_supported_size(int H, int W);
  * when opt leaves cluster_size, kernel and threads at 0: pcs_solve_slices,
  * pcs_solve_slices_weighted and pcs_solve_slices_host then run the row and
  * column kernels of pcs_solve_slices_generic on the context's scratch and
- * stream (asynchronous, no allocation; use_graph has no effect), while FP64
- * reports (rep), pcs_report, pcs_opnorm and monitored solves return
- * PCS_EUNSUPPORTED.
+ * stream (asynchronous, no allocation; use_graph has no effect), rep and
+ * pcs_report give the same FP64 report, and pcs_opnorm and monitored solves
+ * return PCS_EUNSUPPORTED.
  * Errors: PCS_EINVAL (out NULL, max_slices < 1), PCS_EUNSUPPORTED (size),
  *         PCS_ECUDA (no device), PCS_ENOMEM.
  */
@@ -270,14 +270,17 @@ PCS_API pcs_status pcs_field_map(const float *s0, const float *s1, size_t n_voxe
  * b0_axis 0 (B0 along y, the rows axis) or 1 (along x).  D(k) is evaluated
  * in FP32 from the integer frequencies.  field, weight, chi_out: device float32
  * [S][H][W]; mask: device uint8 [S][H][W]; 4-byte alignment suffices; chi_out
- * must not alias field.  Allocates its scratch (4 floats and a half spectrum
- * per pixel), frees it and synchronises cuda_stream before returning.
+ * must not alias field.  rep (host [S], optional): the per-slice FP64 report
+ * of pcs_solve_slices at (chi_N, p_N, q_N).  Allocates its scratch (4 floats
+ * and a half spectrum per pixel), frees it and synchronises cuda_stream before
+ * returning.
  * Errors: PCS_EINVAL for bad arguments, PCS_EUNSUPPORTED for sizes outside
  * the set above, PCS_ECUDA for CUDA failures.  S = 0 is a no-op.
  */
 PCS_API pcs_status pcs_solve_slices_generic(const float *field, const unsigned char *mask, const float *weight,
                                             int S, int H, int W, int b0_axis, double lambda, double tau,
-                                            double sigma, int n_iter, int tv, float *chi_out, void *cuda_stream);
+                                            double sigma, int n_iter, int tv, float *chi_out, pcs_slice_report *rep,
+                                            void *cuda_stream);
 
 /* 1 if pcs_solve_slices_generic accepts H x W slices, else 0. */
 PCS_API int pcs_supported_generic(int H, int W);

@@ -152,7 +152,8 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_slices_weighted": (i, [vp, vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_volume_3d": (i, [vp, vp, vp, i, i, i, d, d, d, i, i, vp, ctypes.POINTER(pcs_slice_report), vp]),
         "pcs_supported_volume_3d": (i, [i, i, i]),
-        "pcs_solve_slices_generic": (i, [vp, vp, vp, i, i, i, i, d, d, d, i, i, vp, vp]),
+        "pcs_solve_slices_generic": (i, [vp, vp, vp, i, i, i, i, d, d, d, i, i, vp, ctypes.POINTER(pcs_slice_report),
+                                         vp]),
         "pcs_supported_generic": (i, [i, i]),
         "pcs_field_map": (i, [vp, vp, ctypes.c_size_t, d, d, d, vp, vp, vp, vp]),
         "pcs_check": (i, [vp]),
@@ -308,9 +309,10 @@ def pcs_solve_volume_3d(field, mask, lam: float, tau: float, sigma: float, n_ite
 
 
 def pcs_solve_slices_generic(field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, tv: int = 0,
-                             weight=None, b0_axis: int = 0, stream=None):
+                             weight=None, b0_axis: int = 0, stream=None, report=False):
     """Per-slice solve for any even H x W with prime factors <= 61 (field/mask/chi_out: [S][H][W]
-    float32/uint8/float32 CUDA tensors; weight: optional float32 data weighting W, default W = mask)."""
+    float32/uint8/float32 CUDA tensors; weight: optional float32 data weighting W, default W = mask).
+    report=True returns the per-slice FP64 reports as a list of dicts."""
     import torch
 
     S, H, W = field.shape
@@ -319,9 +321,11 @@ def pcs_solve_slices_generic(field, mask, lam: float, tau: float, sigma: float, 
     w = None if weight is None else _dev_ptr(weight, "float32", (S, H, W), "weight")
     c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
     st = (stream or torch.cuda.current_stream()).cuda_stream
-    _check(load_library().pcs_solve_slices_generic(f, m, w, S, H, W, b0_axis, lam, tau, sigma, n_iter, tv, c,
+    rep = (pcs_slice_report * S)() if report and S > 0 else None
+    _check(load_library().pcs_solve_slices_generic(f, m, w, S, H, W, b0_axis, lam, tau, sigma, n_iter, tv, c, rep,
                                                    ctypes.c_void_p(st)),
            "pcs_solve_slices_generic")
+    return [r.as_dict() for r in rep] if rep is not None else None
 
 
 def pcs_supported_generic(H: int, W: int) -> bool:

@@ -138,6 +138,9 @@ void gen_destroy(GenSolver* gs);
 cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                         float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
                         double sigma, int n_iter, cudaStream_t st);
+cudaError_t gen_report(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
+                       const float* chi, const float* p, const float* qx, const float* qy, int S, double lambda,
+                       int iters, pcs_slice_report* rep, cudaStream_t st);
 }  // namespace pcs
 
 struct pcs_ctx {
@@ -416,7 +419,13 @@ namespace pcs {
 // (chi, p, q) where p, q are the context's dual state of the last solve.
 pcs_status ctx_report(pcs_ctx* c, const float* field, const unsigned char* mask, int S, double lambda,
                       const float* chi, pcs_slice_report* rep, const float* weight) {
-    if (c->gen) return fail(PCS_EUNSUPPORTED, "FP64 diagnostics need a compiled slice size");
+    if (c->gen) {
+        PCS_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+        PCS_CUDA(gen_report(c->gen, field, mask, weight, chi, c->p, c->qx, c->qy, S, lambda, c->last_iters, rep,
+                            c->stream),
+                 "any-size report");
+        return PCS_OK;
+    }
     pcs_status st = ensure_aux(c);
     if (st != PCS_OK) return st;
     AuxParams a = aux_params(c, S);
@@ -612,7 +621,6 @@ pcs_status pcs_solve_slices(pcs_ctx* ctx, const float* field, const unsigned cha
                             double tau, double sigma, int n_iter, float* chi_out, pcs_slice_report* rep) {
     pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || S == 0) return st;
-    if (rep && ctx->gen) return fail(PCS_EUNSUPPORTED, "FP64 diagnostics need a compiled slice size");
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
     st = launch_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
@@ -626,7 +634,6 @@ pcs_status pcs_solve_slices_weighted(pcs_ctx* ctx, const float* field, const uns
     pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || S == 0) return st;
     if (!weight) return fail(PCS_EINVAL, "weight is NULL");
-    if (rep && ctx->gen) return fail(PCS_EUNSUPPORTED, "FP64 diagnostics need a compiled slice size");
     if (ctx->entry && ctx->entry->resident)
         return fail(PCS_EUNSUPPORTED, "weighted solves run on the streaming kernel (create the context with kernel 1)");
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
@@ -642,7 +649,6 @@ pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const un
                                  pcs_slice_report* rep) {
     pcs_status st = validate_solve(ctx, field_host, mask_host, S, lambda, tau, sigma, n_iter, chi_out_host);
     if (st != PCS_OK || S == 0) return st;
-    if (rep && ctx->gen) return fail(PCS_EUNSUPPORTED, "FP64 diagnostics need a compiled slice size");
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");

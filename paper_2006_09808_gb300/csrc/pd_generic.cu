@@ -2,6 +2,7 @@
 // (pcs_solve_slices_generic; kernels in pd_generic.cuh).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -85,6 +86,7 @@ struct GenSolver {
     GenParams g;  // plans, sizes, tables and spectrum set; state pointers per solve
     float2* tabs = nullptr;
     float2* spec = nullptr;
+    double* partial = nullptr;  // FP64 report: [max_slices][H/2][kGenReportSums]
     int max_slices = 0;
     void (*cols_kern)(GenParams) = nullptr;
     int col_tile = 0, col_threads = 0;
@@ -100,6 +102,7 @@ void gen_destroy(GenSolver* gs) {
     if (!gs) return;
     cudaFree(gs->tabs);
     cudaFree(gs->spec);
+    cudaFree(gs->partial);
     delete gs;
 }
 
@@ -129,9 +132,13 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
     cudaError_t e;
     if ((e = cudaMalloc(&gs->tabs, (size_t)(W + H) * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&gs->spec, (size_t)max_slices * H * M1 * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&gs->partial, (size_t)max_slices * (H / 2) * kGenReportSums * sizeof(double))) !=
+            cudaSuccess ||
         (e = cudaMemcpy(gs->tabs, tw_r.data(), W * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(gs->tabs + W, tw_c.data(), H * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(gen_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->srows)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(gen_report_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->srows)) !=
             cudaSuccess ||
         (e = cudaFuncSetAttribute(gs->cols_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->scols)) !=
             cudaSuccess) {
@@ -197,6 +204,49 @@ cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* 
     return cudaSuccess;
 }
 
+// FP64 diagnostics of every slice at (chi, p, q) (three report launches, two column
+// passes), then a synchronising read-back and fixed-order sums per slice.
+cudaError_t gen_report(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
+                       const float* chi, const float* p, const float* qx, const float* qy, int S, double lambda,
+                       int iters, pcs_slice_report* rep, cudaStream_t st) {
+    GenParams g = gs->g;
+    g.field = field;
+    g.mask = mask;
+    g.weight = weight;
+    g.chi = const_cast<float*>(chi);
+    g.p = const_cast<float*>(p);
+    g.qx = const_cast<float*>(qx);
+    g.qy = const_cast<float*>(qy);
+    g.S = S;
+    const int pairs = S * (g.H / 2);
+    const dim3 grid_r((pairs + kGenRowWarps - 1) / kGenRowWarps);
+    const dim3 grid_c((g.M1 + gs->col_tile - 1) / gs->col_tile, S);
+    cudaError_t e;
+    for (int mode = 0; mode < 3; ++mode) {
+        gen_report_kernel<<<grid_r, kGenRowWarps * 32, gs->srows, st>>>(g, gs->partial, lambda, mode);
+        if (mode < 2) gs->cols_kern<<<grid_c, gs->col_threads, gs->scols, st>>>(g);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    std::vector<double> h((size_t)pairs * kGenReportSums);
+    if ((e = cudaMemcpyAsync(h.data(), gs->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return e;
+    const int PP = g.H / 2;
+    for (int sl = 0; sl < S; ++sl) {
+        double v[kGenReportSums] = {0, 0, 0, 0, 0};
+        for (int q = 0; q < PP; ++q)
+            for (int t = 0; t < kGenReportSums; ++t) v[t] += h[((size_t)sl * PP + q) * kGenReportSums + t];
+        rep[sl].objective = 0.5 * lambda * v[0] + v[1];
+        rep[sl].gap = v[2] / (2.0 * lambda) + v[3];
+        rep[sl].stationarity = std::sqrt(v[4]);
+        rep[sl].data_residual = std::sqrt(v[0]);
+        rep[sl].iters = iters;
+        rep[sl].pad = 0;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace pcs
 
 extern "C" {
@@ -205,7 +255,7 @@ int pcs_supported_generic(int H, int W) { return pcs::gen_supported(H, W) ? 1 : 
 
 pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mask, const float* weight, int S,
                                     int H, int W, int b0_axis, double lambda, double tau, double sigma, int n_iter,
-                                    int tv, float* chi_out, void* cuda_stream) {
+                                    int tv, float* chi_out, pcs_slice_report* rep, void* cuda_stream) {
     if (S < 0) return failg(PCS_EINVAL, "S must be >= 0");
     if (!(lambda > 0.0) || !(tau > 0.0) || !(sigma > 0.0)) return failg(PCS_EINVAL, "lambda, tau, sigma must be > 0");
     if (n_iter < 0) return failg(PCS_EINVAL, "n_iter must be >= 0");
@@ -228,6 +278,9 @@ pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mas
     } else if ((e = pcs::gen_enqueue(gs, field, mask, weight, chi_out, state, state + n, state + 2 * n, state + 3 * n,
                                      S, lambda, tau, sigma, n_iter, st)) != cudaSuccess) {
         ret = failg(PCS_ECUDA, "launch", e);
+    } else if (rep && (e = pcs::gen_report(gs, field, mask, weight, chi_out, state + n, state + 2 * n, state + 3 * n, S,
+                                           lambda, n_iter, rep, st)) != cudaSuccess) {
+        ret = failg(PCS_ECUDA, "report", e);
     }
     // synchronous: the call owns its scratch
     cudaError_t se = cudaStreamSynchronize(st);

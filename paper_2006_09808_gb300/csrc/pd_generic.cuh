@@ -336,6 +336,118 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
     }
 }
 
+// ------------------------------------------------------------------ FP64 diagnostics
+// The terms of the per-slice report at (chi, p, q), per row pair (summed by the host):
+//   [0] ||W (D chi - dB)||^2   [1] TV norm of M G chi   [2] ||p - lambda W (D chi - dB)||^2
+//   [3] sum(|g| - q.g), g = M G chi   [4] ||D W p + G^T M q||^2
+// Three launches with column passes between them: mode 0 forward transforms of chi;
+// mode 1 D chi -> terms 0-3, forward transforms of W p; mode 2 D W p -> term 4.
+constexpr int kGenReportSums = 5;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;  // lane 0
+}
+
+// Two real rows (a: row i0, b: row i1) packed as a + i b -> forward DFT -> half-spectrum rows.
+__device__ __forceinline__ void gen_store_rows(float2* o, float2* scratch, const float2* T, const GenParams& g,
+                                               float2* sp0, float2* sp1, int lane) {
+    const int W = g.W;
+    float2* Z = warp_dft(o, scratch, T, g.prow, false, lane);
+#pragma unroll 3
+    for (int k = lane; k < g.M1; k += 32) {
+        const float2 zk = Z[k], zm = Z[k == 0 ? 0 : W - k];
+        __stcg(sp0 + k, make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y)));
+        __stcg(sp1 + k, make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x)));
+    }
+}
+
+__global__ void __launch_bounds__(kGenRowWarps * 32) gen_report_kernel(GenParams g, double* partial, double lam,
+                                                                        int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = g.H, W = g.W, M1 = g.M1;
+    float2* T = reinterpret_cast<float2*>(smem_raw);
+    for (int t = threadIdx.x; t < W; t += blockDim.x) T[t] = g.trow[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = blockIdx.x * kGenRowWarps + warp;
+    if (pair >= g.S * (H / 2)) return;  // whole warps; no CTA barrier below
+    float2* bufa = T + W + (size_t)warp * 2 * W;
+    float2* bufb = bufa + W;
+    const int s = pair / (H / 2);
+    const int i0 = 2 * (pair - s * (H / 2)), i1 = i0 + 1;
+    const size_t r0 = ((size_t)s * H + i0) * W, r1 = r0 + W;
+    float2* sp0 = g.spec + ((size_t)s * H + i0) * M1;
+    float2* sp1 = sp0 + M1;
+    if (mode == 0) {
+        for (int n = lane; n < W; n += 32) bufa[n] = make_float2(__ldcg(g.chi + r0 + n), __ldcg(g.chi + r1 + n));
+        __syncwarp();
+        gen_store_rows(bufa, bufb, T, g, sp0, sp1, lane);
+        return;
+    }
+    for (int k = lane; k < W; k += 32) {
+        float2 z;
+        if (k < M1) {
+            const float2 A = __ldcg(sp0 + k), B = __ldcg(sp1 + k);
+            z = make_float2(A.x - B.y, A.y + B.x);
+        } else {
+            const float2 A = __ldcg(sp0 + (W - k)), B = __ldcg(sp1 + (W - k));
+            z = make_float2(A.x + B.y, B.x - A.y);
+        }
+        bufa[k] = z;
+    }
+    __syncwarp();
+    float2* u = warp_dft(bufa, bufb, T, g.prow, true, lane);  // D chi (mode 1) or D W p (mode 2)
+    float2* o = (u == bufa) ? bufb : bufa;
+    double acc[kGenReportSums] = {0, 0, 0, 0, 0};
+    for (int n = lane; n < W; n += 32) {
+        const float2 uv = u[n];
+        const float us[2] = {uv.x, uv.y};
+        const int rows[2] = {i0, i1};
+        float wp[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = rows[t];
+            const size_t a = (t == 0 ? r0 : r1) + n;
+            const double m = (double)__ldg(g.mask + a);
+            const double w = g.weight ? (double)__ldg(g.weight + a) : m;
+            const double qx = __ldcg(g.qx + a), qy = __ldcg(g.qy + a);
+            if (mode == 1) {
+                const double c = __ldcg(g.chi + a);
+                const double gx = (n + 1 < W) ? m * ((double)__ldcg(g.chi + a + 1) - c) : 0.0;
+                const double gy = (i + 1 < H) ? m * ((double)__ldcg(g.chi + a + W) - c) : 0.0;
+                const double r = w * ((double)us[t] - (double)__ldg(g.field + a));
+                const double p = __ldcg(g.p + a);
+                const double tvn = g.tv_iso ? sqrt(gx * gx + gy * gy) : fabs(gx) + fabs(gy);
+                acc[0] += r * r;
+                acc[1] += tvn;
+                acc[2] += (p - lam * r) * (p - lam * r);
+                acc[3] += tvn - (qx * gx + qy * gy);
+                wp[t] = (float)(w * p);
+            } else {
+                // G^T (M q): (a[j-1] - a[j] [j < W-1]) + (b[i-1] - b[i] [i < H-1]), a = M qx, b = M qy
+                double k = us[t];
+                if (n > 0) k += (double)__ldg(g.mask + a - 1) * (double)__ldcg(g.qx + a - 1);
+                if (n + 1 < W) k -= m * qx;
+                if (i > 0) k += (double)__ldg(g.mask + a - W) * (double)__ldcg(g.qy + a - W);
+                if (i + 1 < H) k -= m * qy;
+                acc[4] += k * k;
+                wp[t] = 0.f;
+            }
+        }
+        o[n] = make_float2(wp[0], wp[1]);
+    }
+    __syncwarp();
+    double* out = partial + (size_t)pair * kGenReportSums;
+#pragma unroll
+    for (int t = 0; t < kGenReportSums; ++t) {
+        const double v = warp_sum_d(acc[t]);
+        if (lane == 0 && ((mode == 1 && t < 4) || (mode == 2 && t == 4))) out[t] = v;
+    }
+    if (mode == 1) gen_store_rows(o, u, T, g, sp0, sp1, lane);
+}
+
 __device__ __forceinline__ float gen_freq(int k, int n) { return (float)(k < (n + 1) / 2 ? k : k - n) / (float)n; }
 
 // Column kernel: CTA (tile of kGenColTile spectrum columns, slice); one warp per column.

@@ -77,11 +77,11 @@ def test_generic_size_rule(lib):
     for H, W in ((256, 134), (9, 12), (6, 12), (514, 8), (8, 2 * 67), (0, 8)):
         assert lib.pcs_supported_generic(H, W) == 0, (H, W)
     gs = lib.pcs_solve_slices_generic
-    assert gs(None, None, None, 2, 256, 134, 0, 1.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_EUNSUPPORTED
-    assert gs(None, None, None, 2, 256, 258, 0, 1.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_EINVAL  # NULL
-    assert gs(None, None, None, 0, 256, 258, 0, 1.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_OK  # S = 0
-    assert gs(None, None, None, 1, 256, 258, 2, 1.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_EINVAL  # b0_axis
-    assert gs(None, None, None, 1, 256, 258, 0, 0.0, 0.3, 0.3, 5, 0, None, None) == pcs.PCS_EINVAL  # lambda
+    assert gs(None, None, None, 2, 256, 134, 0, 1.0, 0.3, 0.3, 5, 0, None, None, None) == pcs.PCS_EUNSUPPORTED
+    assert gs(None, None, None, 2, 256, 258, 0, 1.0, 0.3, 0.3, 5, 0, None, None, None) == pcs.PCS_EINVAL  # NULL
+    assert gs(None, None, None, 0, 256, 258, 0, 1.0, 0.3, 0.3, 5, 0, None, None, None) == pcs.PCS_OK  # S = 0
+    assert gs(None, None, None, 1, 256, 258, 2, 1.0, 0.3, 0.3, 5, 0, None, None, None) == pcs.PCS_EINVAL  # b0_axis
+    assert gs(None, None, None, 1, 256, 258, 0, 0.0, 0.3, 0.3, 5, 0, None, None, None) == pcs.PCS_EINVAL  # lambda
 
 
 def test_create_without_gpu_reports_cuda_error(lib):

@@ -149,8 +149,8 @@ def test_generic_edge_cases_and_errors():
 
 def test_any_size_context():
     """pcs_create for a size without a compiled kernel makes an any-size context: the same
-    results as pcs_solve_slices_generic, bit for bit, with the context's scratch and stream;
-    repeated solves reuse it; diagnostics are refused before anything is launched."""
+    results and reports as pcs_solve_slices_generic, bit for bit, with the context's scratch
+    and stream; repeated solves reuse it; the power iteration is refused."""
     pb = phantoms.volume(128, 132, 5, seed=75, lam=1.0, n_iter=40)
     direct = gpu_generic(pb.field, pb.mask, 1.0, 40, tv=1)
     f = torch.from_numpy(np.array(pb.field, dtype=np.float32)).cuda()
@@ -171,8 +171,13 @@ def test_any_size_context():
         pcs.pcs_solve_slices_weighted(ctx, f, m, w, 1.0, STEP, STEP, 40, chi)
         stream.synchronize()
         assert rel_l2(chi.cpu().numpy(), oracle(pb.field, pb.mask, 1.0, 40, tv=1, weight=w.cpu().numpy())) <= TOL
-        with pytest.raises(pcs.PcsError) as ei:
-            pcs.pcs_solve_slices(ctx, f, m, 1.0, STEP, STEP, 40, chi, report=True)
+        # the context's FP64 report equals the standalone call's
+        rep = pcs.pcs_solve_slices(ctx, f, m, 1.0, STEP, STEP, 40, chi, report=True)
+        chi2 = torch.empty_like(f)
+        ref = pcs.pcs_solve_slices_generic(f, m, 1.0, STEP, STEP, 40, chi2, tv=1, report=True)
+        assert rep == ref
+        with pytest.raises(pcs.PcsError) as ei:  # the power iteration needs a compiled size
+            pcs.pcs_opnorm(ctx, m, 10)
         assert ei.value.status == pcs.PCS_EUNSUPPORTED
         pcs.pcs_check(ctx)
     finally:
@@ -180,3 +185,50 @@ def test_any_size_context():
     with pytest.raises(pcs.PcsError) as ei:  # a compiled-kernel option cannot apply
         pcs.pcs_create(128, 132, 8, cluster_size=2)
     assert ei.value.status == pcs.PCS_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("H,W,tv,weighted,b0", [(128, 132, 0, False, 0), (256, 258, 1, False, 0),
+                                                (90, 98, 0, True, 1)])
+def test_generic_report_against_oracle(H, W, tv, weighted, b0):
+    """Per-slice FP64 report at (chi_N, p_N, q_N) against the oracle's diagnostics on its own state
+    after the same iterations (gap and stationarity are differences of nearly equal terms: a
+    relative bound plus a floor from the terms' size)."""
+    S, n_iter, lam = 3, 120, 1.0
+    pb = phantoms.volume(H, W, S, seed=81 + H, lam=lam, n_iter=n_iter)
+    w = phantoms.magnitude_weight(pb.mask, seed=82) if weighted else None
+    f = torch.from_numpy(np.array(pb.field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.array(pb.mask, dtype=np.uint8)).cuda()
+    wt = None if w is None else torch.from_numpy(np.array(w, dtype=np.float32)).cuda()
+    chi = torch.empty_like(f)
+    rep = pcs.pcs_solve_slices_generic(f, m, lam, STEP, STEP, n_iter, chi, tv=tv, weight=wt, b0_axis=b0,
+                                       report=True)
+    torch.cuda.synchronize()
+    tvs = "iso" if tv else "aniso"
+    wd = None if w is None else w.astype(np.float64)
+    for s in range(S):
+        st = O.pd_solve(pb.field[s].astype(np.float64), pb.mask[s], lam, STEP, STEP, n_iter, b0_axis=b0,
+                        weight=None if wd is None else wd[s], tv=tvs, return_state=True)
+        ref = O.diagnostics(st, pb.field[s], pb.mask[s], lam, b0_axis=b0, weight=None if wd is None else wd[s],
+                            tv=tvs)
+        r = rep[s]
+        assert r["iters"] == n_iter
+        assert r["objective"] == pytest.approx(ref.primal, rel=1e-4)
+        assert r["data_residual"] == pytest.approx(ref.data_residual, rel=1e-4)
+        assert abs(r["gap"] - ref.gap) <= 2e-2 * ref.gap + 1e-4 * ref.primal
+        assert abs(r["stationarity"] - ref.stationarity) <= 2e-2 * ref.stationarity + 1e-3
+
+
+def test_generic_report_zero_start_closed_form():
+    """N = 0: chi = p = q = 0, so objective = lambda/2 ||W dB||^2, gap = lambda ||W dB||^2 / 2,
+    stationarity 0 and residual ||W dB|| (per slice; no oracle)."""
+    pb = phantoms.volume(128, 132, 2, seed=83, lam=1.0, n_iter=1)
+    lam = 0.25
+    f = torch.from_numpy(np.array(pb.field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.array(pb.mask, dtype=np.uint8)).cuda()
+    rep = pcs.pcs_solve_slices_generic(f, m, lam, STEP, STEP, 0, torch.empty_like(f), report=True)
+    for s in range(2):
+        b2 = float(np.sum((pb.mask[s].astype(np.float64) * pb.field[s].astype(np.float32).astype(np.float64)) ** 2))
+        assert rep[s]["objective"] == pytest.approx(0.5 * lam * b2, rel=1e-12)
+        assert rep[s]["gap"] == pytest.approx(lam * b2 / 2.0, rel=1e-12)
+        assert rep[s]["data_residual"] == pytest.approx(math.sqrt(b2), rel=1e-12)
+        assert rep[s]["stationarity"] == 0.0
