@@ -73,9 +73,15 @@ def dipole_kernel(H: int, W: int, b0_axis: int = 0) -> np.ndarray:
     return D
 
 
-def dipole_kernel_3d(shape, b0_axis: int = 0) -> np.ndarray:
-    """3-D D(k) = 1/3 - k_par^2 / |k|^2, D(0) = 0, B0 along ``b0_axis``."""
-    ks = np.meshgrid(*[np.fft.fftfreq(n) for n in shape], indexing="ij")
+def dipole_kernel_3d(shape, b0_axis: int = 0, voxel=None) -> np.ndarray:
+    """3-D D(k) = 1/3 - k_par^2 / |k|^2, D(0) = 0, B0 along ``b0_axis``.
+
+    ``voxel``: the voxel's edge lengths along the three axes (any unit; None =
+    isotropic).  D depends on the physical frequencies k_i = f_i / voxel_i, f_i in
+    cycles per sample; only their ratios matter.
+    """
+    vox = (1.0, 1.0, 1.0) if voxel is None else tuple(float(v) for v in voxel)
+    ks = np.meshgrid(*[np.fft.fftfreq(n) / v for n, v in zip(shape, vox)], indexing="ij")
     k2 = sum(k * k for k in ks)
     D = np.zeros(shape, dtype=np.float64)
     nz = k2 > 0

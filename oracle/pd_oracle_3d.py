@@ -19,7 +19,11 @@ Readings (the paper is silent on each):
 
 * Volume layout [S][H][W] = (z, y, x); B0 along z, the slice axis
   (``dipole_kernel_3d(shape, b0_axis=0)``): D(k) = 1/3 - kz^2/|k|^2, D(0) = 0,
-  circular on the S x H x W grid, k in cycles per voxel (isotropic voxels).
+  circular on the S x H x W grid.  k is the physical frequency: cycles per
+  sample divided by the voxel's edge along that axis (``voxel`` = (dz, dy, dx),
+  default isotropic; the paper's acquisitions have 0.72 x 0.72 mm pixels and
+  2 mm slices, Sec. III).  G stays the unit forward difference (the paper gives
+  no scaling of it).
 * G: forward differences along x, y and z with a Neumann boundary (zero
   difference on the last column, row and slice); G^T its exact adjoint.
 * The TV dual prox clamps each of the three components (anisotropic);
@@ -91,13 +95,14 @@ def pd_solve_3d(
     theta: float = 1.0,
     return_state: bool = False,
     tv: str = "aniso",
+    voxel=None,
 ):
     """N iterations of the Sec. II.A pseudocode on a whole [S][H][W] volume, in FP64."""
     f = np.asarray(field, dtype=np.float64)
     m = np.asarray(mask, dtype=np.float64)
     Wt = m if weight is None else np.asarray(weight, dtype=np.float64)
     Mt = m if tv_mask is None else np.asarray(tv_mask, dtype=np.float64)
-    Dk = dipole_kernel_3d(f.shape, b0_axis=0)
+    Dk = dipole_kernel_3d(f.shape, b0_axis=0, voxel=voxel)
     b = Wt * f
 
     # zero start, chi_bar_0 = chi_0
@@ -136,6 +141,7 @@ def diagnostics_3d(
     weight: np.ndarray | None = None,
     tv_mask: np.ndarray | None = None,
     tv: str = "aniso",
+    voxel=None,
 ) -> Diagnostics:
     """Objective, Fenchel-Young gap, stationarity and residual of the 3-D problem
     at (chi, p, q) (the same terms as ``pd_oracle.diagnostics``)."""
@@ -143,7 +149,7 @@ def diagnostics_3d(
     m = np.asarray(mask, dtype=np.float64)
     Wt = m if weight is None else np.asarray(weight, dtype=np.float64)
     Mt = m if tv_mask is None else np.asarray(tv_mask, dtype=np.float64)
-    Dk = dipole_kernel_3d(f.shape, b0_axis=0)
+    Dk = dipole_kernel_3d(f.shape, b0_axis=0, voxel=voxel)
     r = Wt * apply_D_3d(state.chi, Dk) - Wt * f
     gx, gy, gz = (Mt * g for g in grad3(state.chi))
     if tv == "iso":
@@ -180,12 +186,13 @@ def opnorm_3d(
     seed: int = 1234,
     weight: np.ndarray | None = None,
     tv_mask: np.ndarray | None = None,
+    voxel=None,
 ) -> float:
     """L = ||K||_2 of the 3-D operator by power iteration on K^T K."""
     m = np.asarray(mask, dtype=np.float64)
     Wt = m if weight is None else np.asarray(weight, dtype=np.float64)
     Mt = m if tv_mask is None else np.asarray(tv_mask, dtype=np.float64)
-    Dk = dipole_kernel_3d(m.shape, b0_axis=0)
+    Dk = dipole_kernel_3d(m.shape, b0_axis=0, voxel=voxel)
     x = np.random.default_rng(seed).standard_normal(m.shape)
     x /= np.linalg.norm(x)
     est = 0.0

@@ -24,15 +24,16 @@ def freq(k, n):
     return k / n if k < (n + 1) // 2 else (k - n) / n
 
 
-def dense_D3(S, H, W):
+def dense_D3(S, H, W, voxel=(1.0, 1.0, 1.0)):
     """F^-1 diag(D) F for the 3-D dipole kernel with B0 along z, built with exp() and the
-    formula 1/3 - fz^2/|f|^2 written out here (no numpy.fft, no oracle kernel)."""
+    formula 1/3 - kz^2/|k|^2 written out here (no numpy.fft, no oracle kernel); k_i is the
+    frequency in cycles per sample over the voxel edge along axis i."""
     N = S * H * W
     idx = list(itertools.product(range(S), range(H), range(W)))
     F = np.empty((N, N), complex)
     d = np.empty(N)
     for r, (kz, ky, kx) in enumerate(idx):
-        fz, fy, fx = freq(kz, S), freq(ky, H), freq(kx, W)
+        fz, fy, fx = freq(kz, S) / voxel[0], freq(ky, H) / voxel[1], freq(kx, W) / voxel[2]
         k2 = fz * fz + fy * fy + fx * fx
         d[r] = 0.0 if k2 == 0 else 1.0 / 3.0 - fz * fz / k2
         for c, (z, y, x) in enumerate(idx):
@@ -55,10 +56,10 @@ def dense_grad3(S, H, W):
     return Gx, Gy, Gz
 
 
-def dense_pd(f, m, w, lam, tau, sigma, n_iter, tv):
+def dense_pd(f, m, w, lam, tau, sigma, n_iter, tv, voxel=(1.0, 1.0, 1.0)):
     """The Sec. II.A pseudocode with explicit matrices on the flattened volume."""
     S, H, W = f.shape
-    D = dense_D3(S, H, W)
+    D = dense_D3(S, H, W, voxel)
     Gx, Gy, Gz = dense_grad3(S, H, W)
     fv, mv, wv = f.ravel(), m.ravel().astype(float), w.ravel()
     n = fv.size
@@ -101,6 +102,38 @@ def test_D3_matches_dense_dft(shape):
     assert np.allclose(got.ravel(), D @ x.ravel(), atol=1e-13)
 
 
+def test_anisotropic_voxel_kernel_hand_fractions():
+    # (4, 6, 8) grid, voxel 2 x 1 x 1: kz = fz / 2.  Index (1, 0, 1): kz = kx = 1/8 -> 1/3 - 1/2;
+    # (1, 1, 0): kz = 1/8, ky = 1/6 -> 1/3 - (1/64) / (1/64 + 1/36) = 1/3 - 9/25 = -2/75;
+    # (2, 0, 2): kz = -1/4, kx = 1/4 -> -1/6; single axes as in the isotropic kernel
+    D = O.dipole_kernel_3d((4, 6, 8), b0_axis=0, voxel=(2.0, 1.0, 1.0))
+    assert D[1, 0, 1] == pytest.approx(-1.0 / 6.0, abs=1e-15)
+    assert D[1, 1, 0] == pytest.approx(-2.0 / 75.0, abs=1e-15)
+    assert D[2, 0, 2] == pytest.approx(-1.0 / 6.0, abs=1e-15)
+    assert D[1, 0, 0] == pytest.approx(-2.0 / 3.0, abs=1e-15)
+    assert D[0, 1, 0] == pytest.approx(1.0 / 3.0, abs=1e-15) and D[0, 0, 0] == 0.0
+    # the isotropic kernel at the same index differs: kz = kx = 1/4 and 1/8 -> 1/3 - 0.8
+    assert O.dipole_kernel_3d((4, 6, 8))[1, 0, 1] == pytest.approx(1.0 / 3.0 - 0.8, abs=1e-15)
+
+
+def test_voxel_scale_invariance():
+    # only the ratios of the voxel edges matter; unit voxels are the isotropic kernel
+    iso = O.dipole_kernel_3d((5, 6, 4))
+    assert np.array_equal(O.dipole_kernel_3d((5, 6, 4), voxel=(1.0, 1.0, 1.0)), iso)
+    assert np.array_equal(O.dipole_kernel_3d((5, 6, 4), voxel=(2.0, 2.0, 2.0)), iso)
+    a = O.dipole_kernel_3d((5, 6, 4), voxel=(2.0, 0.72, 0.72))
+    b = O.dipole_kernel_3d((5, 6, 4), voxel=(4.0, 1.44, 1.44))
+    assert np.allclose(a, b, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("voxel", [(2.0, 0.72, 0.72), (1.0, 3.0, 0.5)])
+def test_D3_anisotropic_matches_dense_dft(voxel):
+    shape = (3, 4, 4)
+    x = np.random.default_rng(4).standard_normal(shape)
+    got = O.apply_D_3d(x, O.dipole_kernel_3d(shape, b0_axis=0, voxel=voxel))
+    assert np.allclose(got.ravel(), dense_D3(*shape, voxel) @ x.ravel(), atol=1e-13)
+
+
 def test_D3_of_z_invariant_field_is_a_third_of_the_deviation():
     # only kz = 0 is present, where D = 1/3 - 0 = 1/3 except at DC (D = 0)
     g = np.random.default_rng(2).standard_normal((8, 6))
@@ -122,6 +155,19 @@ def test_whole_iteration_matches_dense_pseudocode(tv, weighted):
     ref = dense_pd(f, m, w, lam, tau, sigma, n, tv)
     assert np.allclose(got, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
     assert np.abs(ref).max() > 1e-3  # the iteration moved
+
+
+def test_whole_iteration_anisotropic_voxel_matches_dense_pseudocode():
+    rng = np.random.default_rng(5)
+    S, H, W = 3, 4, 4
+    f = rng.standard_normal((S, H, W))
+    m = (rng.random((S, H, W)) > 0.25).astype(np.uint8)
+    vox = (2.0, 0.72, 0.72)
+    got = O3.pd_solve_3d(f, m, 5.0, 0.28, 0.28, 25, voxel=vox)
+    ref = dense_pd(f, m, m.astype(float), 5.0, 0.28, 0.28, 25, "aniso", vox)
+    assert np.allclose(got, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
+    iso = O3.pd_solve_3d(f, m, 5.0, 0.28, 0.28, 25)
+    assert np.abs(got - iso).max() > 1e-3  # the voxel shape changes the result
 
 
 def test_opnorm3_matches_dense_spectral_norm():
@@ -179,8 +225,8 @@ def _mistake_adjoint_z_sign(a, b, c):
     return out
 
 
-def _mistake_b0_along_x(shape, b0_axis=0):
-    return O.dipole_kernel_3d(shape, b0_axis=2)
+def _mistake_b0_along_x(shape, b0_axis=0, voxel=None):
+    return O.dipole_kernel_3d(shape, b0_axis=2, voxel=voxel)
 
 
 @pytest.mark.parametrize(
