@@ -292,7 +292,11 @@ PCS_API int pcs_supported_generic(int H, int W);
  * convolution of the whole volume (Sec. II.A; the per-slice solver above
  * reads G as 2-D and solves slices independently).  The volume [S][H][W] is
  * one unknown: D(k) = 1/3 - kz^2/|k|^2 with B0 along z (the slice axis),
- * periodic on the S x H x W grid, isotropic voxels; G = forward differences
+ * periodic on the S x H x W grid, k_i = (cycles per sample along axis i) /
+ * voxel[i] with voxel = {dz, dy, dx} the voxel's edge lengths in any common
+ * unit (host, optional: NULL = isotropic; the paper's acquisitions have
+ * 0.72 x 0.72 mm pixels and 2 mm slices, Sec. III; each > 0, else
+ * PCS_EINVAL); G = unit forward differences
  * along x, y, z with a Neumann boundary; M = mask, and W = mask when weight
  * is NULL, else weight (device float32 [S][H][W], 16-byte aligned, values in
  * [0, 1], as pcs_solve_slices_weighted).  The Sec. II.A
@@ -313,7 +317,8 @@ PCS_API int pcs_supported_generic(int H, int W);
  */
 PCS_API pcs_status pcs_solve_volume_3d(const float *field, const unsigned char *mask, const float *weight, int S,
                                        int H, int W, double lambda, double tau, double sigma, int n_iter, int tv,
-                                       float *chi_out, pcs_slice_report *rep, void *cuda_stream);
+                                       const double *voxel, float *chi_out, pcs_slice_report *rep,
+                                       void *cuda_stream);
 
 /* 1 if pcs_solve_volume_3d has kernels for an S x H x W volume, else 0. */
 PCS_API int pcs_supported_volume_3d(int S, int H, int W);

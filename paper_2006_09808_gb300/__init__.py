@@ -150,7 +150,8 @@ def load_library(path: str = LIB_PATH):
         "pcs_solve_slices": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_host": (i, [vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
         "pcs_solve_slices_weighted": (i, [vp, vp, vp, vp, i, d, d, d, i, vp, ctypes.POINTER(pcs_slice_report)]),
-        "pcs_solve_volume_3d": (i, [vp, vp, vp, i, i, i, d, d, d, i, i, vp, ctypes.POINTER(pcs_slice_report), vp]),
+        "pcs_solve_volume_3d": (i, [vp, vp, vp, i, i, i, d, d, d, i, i, ctypes.POINTER(d), vp,
+                                    ctypes.POINTER(pcs_slice_report), vp]),
         "pcs_supported_volume_3d": (i, [i, i, i]),
         "pcs_solve_slices_generic": (i, [vp, vp, vp, i, i, i, i, d, d, d, i, i, vp, ctypes.POINTER(pcs_slice_report),
                                          vp]),
@@ -289,10 +290,11 @@ def pcs_solve_slices_weighted(ctx, field, mask, weight, lam: float, tau: float, 
 
 
 def pcs_solve_volume_3d(field, mask, lam: float, tau: float, sigma: float, n_iter: int, chi_out, tv: int = 0,
-                        weight=None, stream=None, report=False):
+                        weight=None, stream=None, report=False, voxel=None):
     """3-D solve of one volume (field/mask/chi_out: [S][H][W] float32/uint8/float32 CUDA tensors;
     weight: optional float32 data weighting W, default W = mask).  report=True returns the
-    volume's FP64 diagnostics as a dict (objective, gap, stationarity, data_residual, iters)."""
+    volume's FP64 diagnostics as a dict (objective, gap, stationarity, data_residual, iters).
+    voxel: optional (dz, dy, dx) voxel edge lengths (default isotropic)."""
     import torch
 
     S, H, W = field.shape
@@ -302,7 +304,8 @@ def pcs_solve_volume_3d(field, mask, lam: float, tau: float, sigma: float, n_ite
     c = _dev_ptr(chi_out, "float32", (S, H, W), "chi_out")
     st = (stream or torch.cuda.current_stream()).cuda_stream
     rep = pcs_slice_report() if report else None
-    _check(load_library().pcs_solve_volume_3d(f, m, w, S, H, W, lam, tau, sigma, n_iter, tv, c,
+    vox = None if voxel is None else (ctypes.c_double * 3)(*[float(v) for v in voxel])
+    _check(load_library().pcs_solve_volume_3d(f, m, w, S, H, W, lam, tau, sigma, n_iter, tv, vox, c,
                                               ctypes.byref(rep) if rep is not None else None, ctypes.c_void_p(st)),
            "pcs_solve_volume_3d")
     return rep.as_dict() if rep is not None else None

@@ -2,6 +2,7 @@
 // (pcs_solve_volume_3d; kernels in pd_3d.cuh).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -62,14 +63,14 @@ const Slice3Entry k_slice3[] = {
 
 struct Z3Entry {
     int NZ, H, W;
-    cudaError_t (*launch)(float2* spec, const float2* twid, int ntw, cudaStream_t st);
+    cudaError_t (*launch)(float2* spec, const float2* twid, int ntw, float3 iv, cudaStream_t st);
 };
 
 template <int NZ, int H, int W>
-cudaError_t launch_z(float2* spec, const float2* twid, int ntw, cudaStream_t st) {
+cudaError_t launch_z(float2* spec, const float2* twid, int ntw, float3 iv, cudaStream_t st) {
     using GZ = GeoZ<NZ, H, W>;
     const dim3 grid(GZ::M + 1, H / GZ::TY);
-    pcs::pd3_z_kernel<GZ, NZ, H, W><<<grid, 256, GZ::SMEM_BYTES, st>>>(spec, twid, ntw);
+    pcs::pd3_z_kernel<GZ, NZ, H, W><<<grid, 256, GZ::SMEM_BYTES, st>>>(spec, twid, ntw, iv);
     return cudaGetLastError();
 }
 
@@ -104,13 +105,20 @@ int pcs_supported_volume_3d(int S, int H, int W) {
 }
 
 pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, const float* weight, int S, int H,
-                               int W, double lambda, double tau, double sigma, int n_iter, int tv, float* chi_out,
-                               pcs_slice_report* rep, void* cuda_stream) {
+                               int W, double lambda, double tau, double sigma, int n_iter, int tv, const double* voxel,
+                               float* chi_out, pcs_slice_report* rep, void* cuda_stream) {
     if (!field || !mask || !chi_out) return fail3(PCS_EINVAL, "NULL argument");
     if (!aligned16(weight)) return fail3(PCS_EINVAL, "weight must be 16-byte aligned");
     if (!(lambda > 0.0) || !(tau > 0.0) || !(sigma > 0.0)) return fail3(PCS_EINVAL, "lambda, tau, sigma must be > 0");
     if (n_iter < 0) return fail3(PCS_EINVAL, "n_iter must be >= 0");
     if (tv != 0 && tv != 1) return fail3(PCS_EINVAL, "tv must be 0 or 1");
+    float3 iv = make_float3(1.f, 1.f, 1.f);  // inverse voxel edges (x, y, z), relative to the smallest
+    if (voxel) {
+        for (int a = 0; a < 3; ++a)
+            if (!(voxel[a] > 0.0) || !std::isfinite(voxel[a])) return fail3(PCS_EINVAL, "voxel edges must be > 0");
+        const double vmin = std::min(voxel[0], std::min(voxel[1], voxel[2]));
+        iv = make_float3((float)(vmin / voxel[2]), (float)(vmin / voxel[1]), (float)(vmin / voxel[0]));
+    }
     if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out))
         return fail3(PCS_EINVAL, "device buffers must be 16-byte aligned");
     if (field == chi_out) return fail3(PCS_EINVAL, "chi_out must not alias field");
@@ -175,7 +183,7 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
             a.phase = 0;
             a.load = it > 0;
             a.store = 1;
-            if ((e = se->launch(a, ncl, st)) != cudaSuccess || (e = ze->launch(spec, twid, ntw, st)) != cudaSuccess) {
+            if ((e = se->launch(a, ncl, st)) != cudaSuccess || (e = ze->launch(spec, twid, ntw, iv, st)) != cudaSuccess) {
                 ret = fail3(PCS_ECUDA, "launch", e);
                 break;
             }
@@ -183,7 +191,7 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
             a.load = 1;
             a.store = it + 1 < n_iter;
             if ((e = se->launch(a, ncl, st)) != cudaSuccess ||
-                (a.store && (e = ze->launch(spec, twid, ntw, st)) != cudaSuccess)) {
+                (a.store && (e = ze->launch(spec, twid, ntw, iv, st)) != cudaSuccess)) {
                 ret = fail3(PCS_ECUDA, "launch", e);
                 break;
             }
@@ -205,7 +213,7 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
                 for (int mode = 0; mode < 3 && ret == PCS_OK; ++mode) {
                     r.mode = mode;
                     if ((e = se->launch_report(r, ncl_rep, st)) != cudaSuccess ||
-                        (mode < 2 && (e = ze->launch(spec, twid, ntw, st)) != cudaSuccess))
+                        (mode < 2 && (e = ze->launch(spec, twid, ntw, iv, st)) != cudaSuccess))
                         ret = fail3(PCS_ECUDA, "report launch", e);
                 }
             }

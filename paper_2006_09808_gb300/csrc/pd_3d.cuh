@@ -276,8 +276,9 @@ __global__ void __launch_bounds__(G::NT, 1) pd3_report_kernel(P3Report r) {
 }
 
 // z pass: pencils of TZ = NZ / EZ lanes, one per (kx, ky); a CTA takes
-// NW * 32 / TZ consecutive ky of one kx.  D(k) = 1/3 - fz^2 / |f|^2 (D(0) = 0)
-// from the integer frequencies, in FP32.
+// NW * 32 / TZ consecutive ky of one kx.  D(k) = 1/3 - kz^2 / |k|^2 (D(0) = 0)
+// in FP32, k_i = f_i * iv_i: the integer frequencies in cycles per sample times the
+// inverse voxel edges (iv = (1, 1, 1) for isotropic voxels).
 template <int NZ, int H, int W, int NT = 256>
 struct GeoZ {
     static constexpr int EZ = default_elems(NZ);
@@ -294,7 +295,7 @@ __device__ __forceinline__ float signed_freq(int k, int n) { return (float)(k < 
 
 template <class GZ, int NZ, int H, int W>
 __global__ void __launch_bounds__(256) pd3_z_kernel(float2* __restrict__ spec, const float2* __restrict__ twid,
-                                                    int ntw) {
+                                                    int ntw, float3 iv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TZ = GZ::TZ, EZ = GZ::EZ, M = GZ::M;
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -314,12 +315,12 @@ __global__ void __launch_bounds__(256) pd3_z_kernel(float2* __restrict__ spec, c
 #pragma unroll
     for (int e = 0; e < EZ; ++e) x[e] = __ldcg(col + (size_t)(g + TZ * e) * stride);
     fft<NZ, TZ, false>(x, pb, stw, g, gm);
-    const float fx = (float)kx / (float)W, fy = signed_freq(ky, H);
+    const float fx = (float)kx / (float)W * iv.x, fy = signed_freq(ky, H) * iv.y;
     const float pxy = fx * fx + fy * fy;
     const float scale = 1.0f / ((float)NZ * (float)H * (float)W);
 #pragma unroll
     for (int e = 0; e < EZ; ++e) {
-        const float fz = signed_freq(g + TZ * e, NZ);
+        const float fz = signed_freq(g + TZ * e, NZ) * iv.z;
         const float k2 = pxy + fz * fz;
         const float d = (k2 > 0.f) ? (1.0f / 3.0f - (fz * fz) / k2) * scale : 0.f;
         x[e] = make_float2(x[e].x * d, x[e].y * d);
