@@ -59,7 +59,7 @@ typedef enum pcs_status {
     PCS_EUNSUPPORTED = 2, /* slice size without a compiled kernel (see pcs_supported_size) */
     PCS_ENOMEM = 3,       /* device allocation failed */
     PCS_ECUDA = 4,        /* a CUDA runtime call failed (no device, launch failure, ...) */
-    PCS_ETIMEOUT = 5,     /* a bounded device wait expired (reserved; no current kernel waits) */
+    PCS_ETIMEOUT = 5,     /* a bounded device wait expired (the balanced schedule's; see pcs_check) */
     PCS_EBUSY = 6         /* context in use by another call */
 } pcs_status;
 
@@ -171,8 +171,9 @@ PCS_API pcs_status pcs_solve_slices_weighted(pcs_ctx *ctx, const float *field, c
  * (about 2 s) and never expected to run out.  If it does, the cluster returns
  * early, the launch's results are invalid and pcs_check reports it.
  *
- * pcs_check: synchronise the context's stream and return PCS_ECUDA if any
- * earlier solve on it gave up a wait (clearing the report), else PCS_OK.
+ * pcs_check: synchronise the context's stream and return PCS_ETIMEOUT if any
+ * earlier solve on it gave up a wait (clearing the report), else PCS_OK
+ * (PCS_ECUDA if the stream reports a CUDA error).
  */
 PCS_API pcs_status pcs_check(pcs_ctx *ctx);
 

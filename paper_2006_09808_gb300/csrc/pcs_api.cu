@@ -588,7 +588,7 @@ pcs_status pcs_check(pcs_ctx* ctx) {
     PCS_CUDA(cudaStreamSynchronize(ctx->stream), "stream sync");
     if (flag) {
         PCS_CUDA(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream), "clear error word");
-        return fail(PCS_ECUDA, "a solve on this context gave up waiting for another cluster (its results are invalid)");
+        return fail(PCS_ETIMEOUT, "a solve on this context gave up waiting for another cluster (its results are invalid)");
     }
     return PCS_OK;
 }
