@@ -232,3 +232,17 @@ def test_generic_report_zero_start_closed_form():
         assert rep[s]["gap"] == pytest.approx(lam * b2 / 2.0, rel=1e-12)
         assert rep[s]["data_residual"] == pytest.approx(math.sqrt(b2), rel=1e-12)
         assert rep[s]["stationarity"] == 0.0
+
+
+def test_solver_on_a_native_size():
+    """The convenience Solver on 128 x 132 slices: steps from the mask-independent bound, the
+    same result as the standalone call with those steps."""
+    pb = phantoms.volume(128, 132, 2, seed=84, lam=1.0, n_iter=30)
+    f = torch.from_numpy(np.array(pb.field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.array(pb.mask, dtype=np.uint8)).cuda()
+    with pcs.Solver(128, 132, 2) as s:
+        L, tau, sigma = s.step_sizes()
+        assert L == pytest.approx(math.sqrt(4.0 / 9.0 + 8.0), rel=1e-15) and tau == sigma
+        chi = s.solve(f, m, 1.0, 30)
+        torch.cuda.synchronize()
+    assert np.array_equal(chi.cpu().numpy(), gpu_generic(pb.field, pb.mask, 1.0, 30))
