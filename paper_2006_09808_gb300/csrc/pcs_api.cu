@@ -15,6 +15,7 @@
 
 #include "../../include/pcs.h"
 #include "pd_launch.cuh"
+#include "pcs_trace.h"
 
 namespace {
 
@@ -484,6 +485,7 @@ pcs_status pcs_options_default(pcs_options* opt) {
 int pcs_supported_size(int H, int W) { return find_entry(H, W, 0) != nullptr ? 1 : 0; }
 
 pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_options* opt, void* cuda_stream) {
+    PCS_TRACE("pcs_create");
     if (!out) return fail(PCS_EINVAL, "out is NULL");
     *out = nullptr;
     if (max_slices < 1) return fail(PCS_EINVAL, "max_slices must be >= 1 (got %d)", max_slices);
@@ -619,6 +621,7 @@ pcs_status pcs_set_stream(pcs_ctx* ctx, void* cuda_stream) {
 
 pcs_status pcs_solve_slices(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
                             double tau, double sigma, int n_iter, float* chi_out, pcs_slice_report* rep) {
+    PCS_TRACE("pcs_solve_slices");
     pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || S == 0) return st;
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
@@ -631,6 +634,7 @@ pcs_status pcs_solve_slices(pcs_ctx* ctx, const float* field, const unsigned cha
 pcs_status pcs_solve_slices_weighted(pcs_ctx* ctx, const float* field, const unsigned char* mask,
                                      const float* weight, int S, double lambda, double tau, double sigma,
                                      int n_iter, float* chi_out, pcs_slice_report* rep) {
+    PCS_TRACE("pcs_solve_slices_weighted");
     pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || S == 0) return st;
     if (!weight) return fail(PCS_EINVAL, "weight is NULL");
@@ -647,6 +651,7 @@ pcs_status pcs_solve_slices_weighted(pcs_ctx* ctx, const float* field, const uns
 pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const unsigned char* mask_host, int S,
                                  double lambda, double tau, double sigma, int n_iter, float* chi_out_host,
                                  pcs_slice_report* rep) {
+    PCS_TRACE("pcs_solve_slices_host");
     pcs_status st = validate_solve(ctx, field_host, mask_host, S, lambda, tau, sigma, n_iter, chi_out_host);
     if (st != PCS_OK || S == 0) return st;
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
@@ -673,6 +678,7 @@ pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const un
 
 pcs_status pcs_report(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S, double lambda,
                       const float* chi, pcs_slice_report* rep) {
+    PCS_TRACE("pcs_report");
     if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
     if (S < 0 || S > ctx->max_slices) return fail(PCS_EINVAL, "S=%d outside [0, max_slices]", S);
     if (S == 0) return PCS_OK;
@@ -682,6 +688,7 @@ pcs_status pcs_report(pcs_ctx* ctx, const float* field, const unsigned char* mas
 }
 
 pcs_status pcs_opnorm(pcs_ctx* ctx, const unsigned char* mask, int S, int power_iters, double* L_out) {
+    PCS_TRACE("pcs_opnorm");
     if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
     if (S < 0 || S > ctx->max_slices) return fail(PCS_EINVAL, "S=%d outside [0, max_slices]", S);
     if (S == 0) return PCS_OK;
@@ -693,6 +700,7 @@ pcs_status pcs_opnorm(pcs_ctx* ctx, const unsigned char* mask, int S, int power_
 pcs_status pcs_solve_slices_monitored(pcs_ctx* ctx, const float* field, const unsigned char* mask, int S,
                                       double lambda, double tau, double sigma, int n_iter, int check_every,
                                       double rel_gap_tol, float* chi_out, pcs_slice_report* rep) {
+    PCS_TRACE("pcs_solve_slices_monitored");
     pcs_status st = validate_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || S == 0) return st;
     if (!rep) return fail(PCS_EINVAL, "rep is required");
@@ -916,6 +924,7 @@ pcs_status pcs_batch_create(pcs_batch** out, const pcs_options* opt, int autotun
 }
 
 pcs_status pcs_batch_solve(pcs_batch* b, const pcs_volume* vols, int n_vols, int n_iter) {
+    PCS_TRACE("pcs_batch_solve");
     if (!b) return fail(PCS_EINVAL, "batch is NULL");
     if (n_vols < 0 || (n_vols > 0 && !vols)) return fail(PCS_EINVAL, "bad volume list");
     if (n_iter < 0) return fail(PCS_EINVAL, "n_iter must be >= 0");
@@ -1021,6 +1030,7 @@ void pcs_batch_destroy(pcs_batch* b) {
 extern "C" pcs_status pcs_solve_slices_f64(const double* field, const unsigned char* mask, int H, int W, int S,
                                            double lambda, double tau, double sigma, int n_iter, double* chi_out,
                                            int b0_axis, void* cuda_stream) {
+    PCS_TRACE("pcs_solve_slices_f64");
     if (S < 0 || n_iter < 0) return fail(PCS_EINVAL, "S and n_iter must be >= 0");
     const pcs::KernelEntryF64* entry = nullptr;
     int ne = 0;

@@ -18,6 +18,7 @@
 #include <cstdio>
 
 #include "../../include/pcs.h"
+#include "pcs_trace.h"
 
 namespace pcs {
 pcs_status set_last_error(pcs_status st, const char* msg);
@@ -116,6 +117,7 @@ pcs_status fm_fail(pcs_status st, const char* what, cudaError_t e = cudaSuccess)
 extern "C" pcs_status pcs_field_map(const float* s0, const float* s1, size_t n_voxels, double t_shift_s,
                                     double b0_tesla, double threshold, float* field_out, float* weight_out,
                                     unsigned char* mask_out, void* cuda_stream) {
+    PCS_TRACE("pcs_field_map");
     if (n_voxels == 0) return PCS_OK;
     if (!s0 || !s1 || !field_out || !weight_out || !mask_out) return fm_fail(PCS_EINVAL, "NULL argument");
     if (!(t_shift_s > 0.0) || !(b0_tesla > 0.0) || !(threshold >= 0.0))

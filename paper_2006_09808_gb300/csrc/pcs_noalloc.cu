@@ -31,6 +31,7 @@
 
 #include "../../include/pcs.h"
 #include "pd_launch.cuh"
+#include "pcs_trace.h"
 
 namespace pcs {
 void build_dipole_tables(int H, int W, int b0_axis, std::vector<float>& dtab, std::vector<float>& ddtab);
@@ -88,6 +89,7 @@ const pcs::KernelEntry* default_entry(int H, int W) {
 extern "C" pcs_status pcs_solve_slices_noalloc(const float* field, const unsigned char* mask, int H, int W,
                                                int S, double lambda, double tau, double sigma, int n_iter,
                                                float* chi_out, int b0_axis, void* cuda_stream) {
+    PCS_TRACE("pcs_solve_slices_noalloc");
     if (S < 0 || n_iter < 0) return pcs::set_last_error(PCS_EINVAL, "pcs_solve_slices_noalloc: S and n_iter must be >= 0");
     const pcs::KernelEntry* entry = default_entry(H, W);
     if (!entry) return pcs::set_last_error(PCS_EUNSUPPORTED, "pcs_solve_slices_noalloc: unsupported slice size");

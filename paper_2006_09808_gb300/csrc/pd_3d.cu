@@ -11,6 +11,7 @@
 #include "../../include/pcs.h"
 #include "pd_3d.cuh"
 #include "pd_launch.cuh"
+#include "pcs_trace.h"
 
 namespace pcs {
 void build_twiddles(int n, std::vector<float2>& tw);
@@ -107,6 +108,7 @@ int pcs_supported_volume_3d(int S, int H, int W) {
 pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, const float* weight, int S, int H,
                                int W, double lambda, double tau, double sigma, int n_iter, int tv, const double* voxel,
                                float* chi_out, pcs_slice_report* rep, void* cuda_stream) {
+    PCS_TRACE("pcs_solve_volume_3d");
     if (!field || !mask || !chi_out) return fail3(PCS_EINVAL, "NULL argument");
     if (!aligned16(weight)) return fail3(PCS_EINVAL, "weight must be 16-byte aligned");
     if (!(lambda > 0.0) || !(tau > 0.0) || !(sigma > 0.0)) return fail3(PCS_EINVAL, "lambda, tau, sigma must be > 0");

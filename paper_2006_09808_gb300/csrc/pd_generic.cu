@@ -9,6 +9,7 @@
 
 #include "../../include/pcs.h"
 #include "pd_generic.cuh"
+#include "pcs_trace.h"
 
 namespace pcs {
 void build_twiddles(int n, std::vector<float2>& tw);
@@ -256,6 +257,7 @@ int pcs_supported_generic(int H, int W) { return pcs::gen_supported(H, W) ? 1 : 
 pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mask, const float* weight, int S,
                                     int H, int W, int b0_axis, double lambda, double tau, double sigma, int n_iter,
                                     int tv, float* chi_out, pcs_slice_report* rep, void* cuda_stream) {
+    PCS_TRACE("pcs_solve_slices_generic");
     if (S < 0) return failg(PCS_EINVAL, "S must be >= 0");
     if (!(lambda > 0.0) || !(tau > 0.0) || !(sigma > 0.0)) return failg(PCS_EINVAL, "lambda, tau, sigma must be > 0");
     if (n_iter < 0) return failg(PCS_EINVAL, "n_iter must be >= 0");
