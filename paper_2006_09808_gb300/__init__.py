@@ -567,19 +567,13 @@ class Solver:
         self._L = None
 
     def step_sizes(self, power_iters: int = 300):
-        """(L, tau, sigma) with tau = sigma = 1/L: L = ||K|| of the full-mask operator of this slice
-        size by the device power iteration; for sizes without a compiled kernel (any-size contexts)
-        the mask-independent bound sqrt(4/9 + 8) (||D|| <= 2/3, ||G||^2 <= 8)."""
-        import math
-
+        """(L, tau, sigma) with tau = sigma = 1/L for the full-mask operator of this slice size
+        (device power iteration)."""
         import torch
 
         if self._L is None:
-            if pcs_supported_size(self.H, self.W):
-                ones = torch.ones((1, self.H, self.W), dtype=torch.uint8, device="cuda")
-                self._L = pcs_opnorm(self.ctx, ones, power_iters)[0]
-            else:
-                self._L = math.sqrt(4.0 / 9.0 + 8.0)
+            ones = torch.ones((1, self.H, self.W), dtype=torch.uint8, device="cuda")
+            self._L = pcs_opnorm(self.ctx, ones, power_iters)[0]
         return self._L, 1.0 / self._L, 1.0 / self._L
 
     def solve(self, field, mask, lam: float, n_iter: int, tau: float | None = None, sigma: float | None = None,

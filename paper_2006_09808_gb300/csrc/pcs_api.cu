@@ -142,6 +142,8 @@ cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* 
 cudaError_t gen_report(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                        const float* chi, const float* p, const float* qx, const float* qy, int S, double lambda,
                        int iters, pcs_slice_report* rep, cudaStream_t st);
+cudaError_t gen_opnorm(GenSolver* gs, const unsigned char* mask, int S, int power_iters, double* L_out,
+                       cudaStream_t st);
 }  // namespace pcs
 
 struct pcs_ctx {
@@ -458,7 +460,11 @@ pcs_status ctx_report(pcs_ctx* c, const float* field, const unsigned char* mask,
 }
 
 pcs_status ctx_opnorm(pcs_ctx* c, const unsigned char* mask, int S, int power_iters, double* L_out) {
-    if (c->gen) return fail(PCS_EUNSUPPORTED, "the power iteration needs a compiled slice size");
+    if (c->gen) {
+        PCS_CUDA(cudaSetDevice(c->device), "cudaSetDevice");
+        PCS_CUDA(gen_opnorm(c->gen, mask, S, power_iters, L_out, c->stream), "any-size power iteration");
+        return PCS_OK;
+    }
     pcs_status st = ensure_aux(c);
     if (st != PCS_OK) return st;
     AuxParams a = aux_params(c, S);

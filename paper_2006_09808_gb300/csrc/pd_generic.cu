@@ -141,6 +141,8 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
             cudaSuccess ||
         (e = cudaFuncSetAttribute(gen_report_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->srows)) !=
             cudaSuccess ||
+        (e = cudaFuncSetAttribute(gen_opnorm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)gs->srows)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(gs->cols_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->scols)) !=
             cudaSuccess) {
         gen_destroy(gs);
@@ -246,6 +248,55 @@ cudaError_t gen_report(GenSolver* gs, const float* field, const unsigned char* m
         rep[sl].pad = 0;
     }
     return cudaSuccess;
+}
+
+// L = ||K|| of every slice's operator (W = M = mask) by power_iters steps of the power
+// iteration on K^T K from a fixed pseudo-random start; synchronises st.
+cudaError_t gen_opnorm(GenSolver* gs, const unsigned char* mask, int S, int power_iters, double* L_out,
+                       cudaStream_t st) {
+    GenParams g = gs->g;
+    g.mask = mask;
+    g.S = S;
+    const size_t n = (size_t)S * g.H * g.W;
+    const int pairs = S * (g.H / 2);
+    const dim3 grid_r((pairs + kGenRowWarps - 1) / kGenRowWarps);
+    const dim3 grid_c((g.M1 + gs->col_tile - 1) / gs->col_tile, S);
+    const dim3 grid_n((S + 127) / 128);
+    float* buf = nullptr;  // x, y [n] each, scale [S]
+    double* est = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&buf, (2 * n + S) * sizeof(float))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&est, (size_t)S * sizeof(double))) != cudaSuccess) {
+        cudaFree(buf);
+        return e;
+    }
+    float* x = buf;
+    float* y = buf + n;
+    float* scale = buf + 2 * n;
+    gen_opnorm_init_kernel<<<grid_r, kGenRowWarps * 32, 0, st>>>(g, x, gs->partial);
+    gen_opnorm_norm_kernel<<<grid_n, 128, 0, st>>>(gs->partial, g.H / 2, S, scale, est);
+    for (int it = 0; it < power_iters; ++it) {
+        gen_opnorm_rows_kernel<<<grid_r, kGenRowWarps * 32, gs->srows, st>>>(g, x, y, scale, gs->partial, 0);
+        gs->cols_kern<<<grid_c, gs->col_threads, gs->scols, st>>>(g);
+        gen_opnorm_rows_kernel<<<grid_r, kGenRowWarps * 32, gs->srows, st>>>(g, x, y, scale, gs->partial, 1);
+        gs->cols_kern<<<grid_c, gs->col_threads, gs->scols, st>>>(g);
+        gen_opnorm_rows_kernel<<<grid_r, kGenRowWarps * 32, gs->srows, st>>>(g, x, y, scale, gs->partial, 2);
+        gen_opnorm_norm_kernel<<<grid_n, 128, 0, st>>>(gs->partial, g.H / 2, S, scale, est);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        float* t = x;
+        x = y;
+        y = t;
+    }
+    std::vector<double> h(S);
+    if (e == cudaSuccess &&
+        (e = cudaMemcpyAsync(h.data(), est, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess)
+        for (int sl = 0; sl < S; ++sl) L_out[sl] = std::sqrt(h[sl] > 0.0 ? h[sl] : 0.0);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    cudaFree(est);
+    return e;
 }
 
 }  // namespace pcs

@@ -448,6 +448,140 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_report_kernel(GenParams
     if (mode == 1) gen_store_rows(o, u, T, g, sp0, sp1, lane);
 }
 
+// ------------------------------------------------------------------ power iteration for L = ||K||
+// Per slice, x <- K^T K x / ||K^T K x|| with K^T K x = D M^2 D x + G^T M^2 G x (W = M = mask).
+// The stored vector is unnormalised; scale[s] turns it into the unit vector.  Per iteration:
+// mode 0 forward transforms of scale x; column pass; mode 1 D x -> M^2 D x -> forward;
+// column pass; mode 2 y = D M^2 D x + G^T M^2 G x with <x, y> and ||y||^2 per row pair;
+// then gen_opnorm_norm_kernel: est = <x, y>, scale = 1 / ||y||.
+
+// Deterministic start vector in [-1, 1) from the voxel index (splitmix64 finaliser).
+__device__ __forceinline__ float gen_hash_unit(unsigned long long k) {
+    k += 0x9E3779B97F4A7C15ull;
+    k = (k ^ (k >> 30)) * 0xBF58476D1CE4E5B9ull;
+    k = (k ^ (k >> 27)) * 0x94D049BB133111EBull;
+    k ^= k >> 31;
+    return (float)((double)(k >> 40) * (1.0 / 8388608.0) - 1.0);
+}
+
+__global__ void __launch_bounds__(kGenRowWarps * 32) gen_opnorm_init_kernel(GenParams g, float* x, double* partial) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = blockIdx.x * kGenRowWarps + warp;
+    if (pair >= g.S * (g.H / 2)) return;
+    const size_t r0 = (size_t)pair * 2 * g.W;  // rows 2 pr, 2 pr + 1 of the slices laid end to end
+    double nn = 0.0;
+    for (int n = lane; n < 2 * g.W; n += 32) {
+        const float v = gen_hash_unit(r0 + n);
+        x[r0 + n] = v;
+        nn += (double)v * v;
+    }
+    nn = warp_sum_d(nn);
+    if (lane == 0) {
+        partial[2 * (size_t)pair] = 0.0;
+        partial[2 * (size_t)pair + 1] = nn;
+    }
+}
+
+// est[s] = sum of the slice's <x, y> partials, scale[s] = 1 / sqrt(sum of ||y||^2), fixed order.
+__global__ void gen_opnorm_norm_kernel(const double* partial, int pairs_per_slice, int S, float* scale,
+                                       double* est) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double xy = 0.0, yy = 0.0;
+    for (int q = 0; q < pairs_per_slice; ++q) {
+        xy += partial[2 * ((size_t)s * pairs_per_slice + q)];
+        yy += partial[2 * ((size_t)s * pairs_per_slice + q) + 1];
+    }
+    est[s] = xy;
+    scale[s] = (yy > 0.0) ? (float)(1.0 / sqrt(yy)) : 0.f;
+}
+
+__global__ void __launch_bounds__(kGenRowWarps * 32) gen_opnorm_rows_kernel(GenParams g, const float* x, float* y,
+                                                                             const float* scale, double* partial,
+                                                                             int mode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = g.H, W = g.W, M1 = g.M1;
+    float2* T = reinterpret_cast<float2*>(smem_raw);
+    for (int t = threadIdx.x; t < W; t += blockDim.x) T[t] = g.trow[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = blockIdx.x * kGenRowWarps + warp;
+    if (pair >= g.S * (H / 2)) return;  // whole warps; no CTA barrier below
+    float2* bufa = T + W + (size_t)warp * 2 * W;
+    float2* bufb = bufa + W;
+    const int s = pair / (H / 2);
+    const int i0 = 2 * (pair - s * (H / 2)), i1 = i0 + 1;
+    const size_t r0 = ((size_t)s * H + i0) * W, r1 = r0 + W;
+    float2* sp0 = g.spec + ((size_t)s * H + i0) * M1;
+    float2* sp1 = sp0 + M1;
+    const float sc = scale[s];
+    if (mode == 0) {
+        for (int n = lane; n < W; n += 32) bufa[n] = make_float2(sc * x[r0 + n], sc * x[r1 + n]);
+        __syncwarp();
+        gen_store_rows(bufa, bufb, T, g, sp0, sp1, lane);
+        return;
+    }
+    for (int k = lane; k < W; k += 32) {
+        float2 z;
+        if (k < M1) {
+            const float2 A = __ldcg(sp0 + k), B = __ldcg(sp1 + k);
+            z = make_float2(A.x - B.y, A.y + B.x);
+        } else {
+            const float2 A = __ldcg(sp0 + (W - k)), B = __ldcg(sp1 + (W - k));
+            z = make_float2(A.x + B.y, B.x - A.y);
+        }
+        bufa[k] = z;
+    }
+    __syncwarp();
+    float2* u = warp_dft(bufa, bufb, T, g.prow, true, lane);
+    float2* o = (u == bufa) ? bufb : bufa;
+    if (mode == 1) {
+        for (int n = lane; n < W; n += 32) {
+            const float m0 = (float)__ldg(g.mask + r0 + n), m1 = (float)__ldg(g.mask + r1 + n);
+            o[n] = make_float2(u[n].x * m0 * m0, u[n].y * m1 * m1);
+        }
+        __syncwarp();
+        gen_store_rows(o, u, T, g, sp0, sp1, lane);
+        return;
+    }
+    // mode 2: y = D M^2 D x + G^T M^2 G x at rows i0, i1
+    auto X = [&](size_t idx) { return sc * x[idx]; };
+    auto M2 = [&](size_t idx) {
+        const float m = (float)__ldg(g.mask + idx);
+        return m * m;
+    };
+    const size_t sbase = (size_t)s * H * W;
+    auto ax = [&](int ii, int jj) -> float {  // M^2 gx at (ii, jj)
+        if (jj < 0 || jj >= W - 1) return 0.f;
+        const size_t q = sbase + (size_t)ii * W + jj;
+        return M2(q) * (X(q + 1) - X(q));
+    };
+    auto by = [&](int ii, int jj) -> float {  // M^2 gy at (ii, jj)
+        if (ii < 0 || ii >= H - 1) return 0.f;
+        const size_t q = sbase + (size_t)ii * W + jj;
+        return M2(q) * (X(q + W) - X(q));
+    };
+    double xy = 0.0, yy = 0.0;
+    for (int n = lane; n < W; n += 32) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = t == 0 ? i0 : i1;
+            const size_t q = (t == 0 ? r0 : r1) + n;
+            const float gt = (ax(i, n - 1) - ax(i, n)) + (by(i - 1, n) - by(i, n));
+            const float v = (t == 0 ? u[n].x : u[n].y) + gt;
+            y[q] = v;
+            xy += (double)X(q) * v;
+            yy += (double)v * v;
+        }
+    }
+    xy = warp_sum_d(xy);
+    yy = warp_sum_d(yy);
+    if (lane == 0) {
+        partial[2 * (size_t)pair] = xy;
+        partial[2 * (size_t)pair + 1] = yy;
+    }
+}
+
 __device__ __forceinline__ float gen_freq(int k, int n) { return (float)(k < (n + 1) / 2 ? k : k - n) / (float)n; }
 
 // Column kernel: CTA (tile of kGenColTile spectrum columns, slice); one warp per column.
