@@ -111,7 +111,9 @@ PCS_API int pcs_supported_size(int H, int W);
  * column kernels of pcs_solve_slices_generic on the context's scratch and
  * stream (asynchronous, no allocation; use_graph has no effect), rep and
  * pcs_report give the same FP64 report, pcs_opnorm runs the same power
- * iteration with these kernels, and monitored solves return PCS_EUNSUPPORTED.
+ * iteration with these kernels, and pcs_solve_slices_monitored resumes from
+ * the stored state (the spectrum of chibar rebuilt) with frozen slices left
+ * alone.
  * Errors: PCS_EINVAL (out NULL, max_slices < 1), PCS_EUNSUPPORTED (size),
  *         PCS_ECUDA (no device), PCS_ENOMEM.
  */

@@ -138,7 +138,7 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
 void gen_destroy(GenSolver* gs);
 cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                         float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
-                        double sigma, int n_iter, cudaStream_t st);
+                        double sigma, int n_iter, cudaStream_t st, int resume, const int* active);
 cudaError_t gen_report(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                        const float* chi, const float* p, const float* qx, const float* qy, int S, double lambda,
                        int iters, pcs_slice_report* rep, cudaStream_t st);
@@ -261,11 +261,10 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out) || !aligned16(weight))
         return fail(PCS_EINVAL, "device buffers must be 16-byte aligned");
     if (ctx->gen) {
-        if (inv_den_slice || entry || resume || active)
-            return fail(PCS_EUNSUPPORTED, "per-slice lambdas, resumed and monitored solves need a compiled size");
+        if (inv_den_slice || entry) return fail(PCS_EUNSUPPORTED, "per-slice lambdas need a compiled size");
         PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
         PCS_CUDA(pcs::gen_enqueue(ctx->gen, field, mask, weight, chi_out, ctx->chibar, ctx->p, ctx->qx, ctx->qy, S,
-                                  lambda, tau, sigma, n_iter, ctx->stream),
+                                  lambda, tau, sigma, n_iter, ctx->stream, resume, active),
                  "launch of the any-size kernels");
         ctx->last_iters = n_iter;
         return PCS_OK;
@@ -712,17 +711,21 @@ pcs_status pcs_solve_slices_monitored(pcs_ctx* ctx, const float* field, const un
     if (!rep) return fail(PCS_EINVAL, "rep is required");
     if (check_every < 1) return fail(PCS_EINVAL, "check_every must be >= 1");
     if (!(rel_gap_tol >= 0.0)) return fail(PCS_EINVAL, "rel_gap_tol must be >= 0");
-    if (ctx->gen) return fail(PCS_EUNSUPPORTED, "monitored solves need a compiled slice size");
     std::unique_lock<std::mutex> lk(ctx->mu, std::try_to_lock);
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    // chunked solves resume from the stored state: a streaming variant of this size
-    const pcs::KernelEntry* e = ctx->entry->resident ? find_entry(ctx->H, ctx->W, 0, 1) : ctx->entry;
-    if (!e) return fail(PCS_EUNSUPPORTED, "no streaming kernel for %d x %d", ctx->H, ctx->W);
-    int ncl = ctx->max_clusters;
-    if (e != ctx->entry) {
-        int aux = 0;
-        PCS_CUDA(e->prepare(&ncl, &aux), "kernel attributes");
+    // chunked solves resume from the stored state: a streaming variant of this size (any-size
+    // contexts resume with their own kernels)
+    const pcs::KernelEntry* e = nullptr;
+    int ncl = 0;
+    if (!ctx->gen) {
+        e = ctx->entry->resident ? find_entry(ctx->H, ctx->W, 0, 1) : ctx->entry;
+        if (!e) return fail(PCS_EUNSUPPORTED, "no streaming kernel for %d x %d", ctx->H, ctx->W);
+        ncl = ctx->max_clusters;
+        if (e != ctx->entry) {
+            int aux = 0;
+            PCS_CUDA(e->prepare(&ncl, &aux), "kernel attributes");
+        }
     }
     if (!ctx->active) PCS_CUDA(cudaMalloc(&ctx->active, (size_t)ctx->max_slices * sizeof(int)), "cudaMalloc flags");
     std::vector<int> act(S, 1);

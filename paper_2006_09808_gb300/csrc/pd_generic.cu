@@ -161,21 +161,25 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
     return cudaSuccess;
 }
 
-// Enqueue a solve of S <= max_slices slices on st: zero state, chi and spectrum, then
-// n_iter iterations of four launches.  Asynchronous; no allocation.
+// Enqueue a solve of S <= max_slices slices on st: zero state, chi and spectrum (or, with
+// resume, continue from the stored chi, chibar, p, q: the spectrum D F chibar is rebuilt),
+// then n_iter iterations of four launches; slices with active[s] = 0 stay as they are.
+// Asynchronous; no allocation.
 cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                         float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
-                        double sigma, int n_iter, cudaStream_t st) {
+                        double sigma, int n_iter, cudaStream_t st, int resume, const int* active) {
     GenParams g = gs->g;
     const size_t n = (size_t)S * g.H * g.W;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(chibar, 0, n * sizeof(float), st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p, 0, n * sizeof(float), st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(qx, 0, n * sizeof(float), st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(qy, 0, n * sizeof(float), st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(chi, 0, n * sizeof(float), st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(g.spec, 0, (size_t)S * g.H * g.M1 * sizeof(float2), st)) != cudaSuccess)
+    if (!resume &&
+        ((e = cudaMemsetAsync(chibar, 0, n * sizeof(float), st)) != cudaSuccess ||
+         (e = cudaMemsetAsync(p, 0, n * sizeof(float), st)) != cudaSuccess ||
+         (e = cudaMemsetAsync(qx, 0, n * sizeof(float), st)) != cudaSuccess ||
+         (e = cudaMemsetAsync(qy, 0, n * sizeof(float), st)) != cudaSuccess ||
+         (e = cudaMemsetAsync(chi, 0, n * sizeof(float), st)) != cudaSuccess ||
+         (e = cudaMemsetAsync(g.spec, 0, (size_t)S * g.H * g.M1 * sizeof(float2), st)) != cudaSuccess))
         return e;
+    g.active = active;
     g.field = field;
     g.mask = mask;
     g.weight = weight;
@@ -191,6 +195,13 @@ cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* 
     const int pairs = S * (g.H / 2);
     const dim3 grid_r((pairs + kGenRowWarps - 1) / kGenRowWarps);
     const dim3 grid_c((g.M1 + gs->col_tile - 1) / gs->col_tile, S);
+    if (resume && n_iter > 0) {
+        // forward transforms of the stored chibar (the report kernel's first mode), column pass
+        GenParams r = g;
+        r.chi = chibar;
+        gen_report_kernel<<<grid_r, kGenRowWarps * 32, gs->srows, st>>>(r, gs->partial, lambda, 0);
+        gs->cols_kern<<<grid_c, gs->col_threads, gs->scols, st>>>(g);
+    }
     // iteration n: dual step from the spectrum D F chibar_n (zero at n = 0), column pass
     // (spectrum of W p), primal step, column pass (spectrum of chibar_{n+1}; not after the last)
     for (int it = 0; it < n_iter; ++it) {
@@ -329,7 +340,7 @@ pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mas
         (e = cudaMalloc(&state, 4 * n * sizeof(float))) != cudaSuccess) {
         ret = failg(PCS_ECUDA, "set-up", e);
     } else if ((e = pcs::gen_enqueue(gs, field, mask, weight, chi_out, state, state + n, state + 2 * n, state + 3 * n,
-                                     S, lambda, tau, sigma, n_iter, st)) != cudaSuccess) {
+                                     S, lambda, tau, sigma, n_iter, st, 0, nullptr)) != cudaSuccess) {
         ret = failg(PCS_ECUDA, "launch", e);
     } else if (rep && (e = pcs::gen_report(gs, field, mask, weight, chi_out, state + n, state + 2 * n, state + 3 * n, S,
                                            lambda, n_iter, rep, st)) != cudaSuccess) {

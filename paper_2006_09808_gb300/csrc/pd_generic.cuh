@@ -50,6 +50,7 @@ struct GenParams {
     int b0_axis;           // 0: B0 along y (rows), 1: along x
     int phase;             // 0: dual step, 1: primal step
     int store;             // 1: forward transforms of the phase's output to the spectrum
+    const int* active;     // NULL, or per-slice flags: 0 = frozen (the row kernel leaves it alone)
 };
 
 __device__ __forceinline__ float2 gcmul(float2 a, float2 b) {
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
     float2* bufa = T + W + (size_t)warp * 2 * W;
     float2* bufb = bufa + W;
     const int s = pair / (H / 2);
+    if (g.active && !g.active[s]) return;  // frozen slice (monitored solves): state kept as is
     const int i0 = 2 * (pair - s * (H / 2)), i1 = i0 + 1;
     const size_t r0 = ((size_t)s * H + i0) * W, r1 = r0 + W;
     float2* sp0 = g.spec + ((size_t)s * H + i0) * M1;

@@ -262,3 +262,34 @@ def test_solver_on_a_native_size():
     pcs.pcs_solve_slices_generic(f, m, 1.0, tau, sigma, 30, chi2)
     torch.cuda.synchronize()
     assert np.array_equal(chi.cpu().numpy(), chi2.cpu().numpy())
+
+
+def test_generic_monitored_resume_and_early_stop():
+    """Monitored solves on an any-size context: chunks of 25 iterations resume exactly (equal bit
+    for bit to one straight solve, reports included), and a slice whose gap is already zero (zero
+    field) freezes at the first check while the others run on."""
+    pb = phantoms.volume(128, 132, 3, seed=85, lam=1.0, n_iter=75)
+    field = np.array(pb.field, dtype=np.float32)
+    field[1] = 0.0  # chi stays 0: gap 0 at every check
+    f = torch.from_numpy(field).cuda()
+    m = torch.from_numpy(np.array(pb.mask, dtype=np.uint8)).cuda()
+    ctx = pcs.pcs_create(128, 132, 3)
+    try:
+        straight = torch.empty_like(f)
+        rep_s = pcs.pcs_solve_slices(ctx, f, m, 1.0, STEP, STEP, 75, straight, report=True)
+        chunked = torch.full_like(f, float("nan"))
+        rep_c = pcs.pcs_solve_slices_monitored(ctx, f, m, 1.0, STEP, STEP, 75, 25, 0.0, chunked)
+        torch.cuda.synchronize()
+        assert np.array_equal(chunked.cpu().numpy(), straight.cpu().numpy())
+        for a, b in zip(rep_c, rep_s):
+            assert a == b
+        stop = torch.full_like(f, float("nan"))
+        rep_e = pcs.pcs_solve_slices_monitored(ctx, f, m, 1.0, STEP, STEP, 75, 25, 1e-12, stop)
+        torch.cuda.synchronize()
+    finally:
+        pcs.pcs_destroy(ctx)
+    assert rep_e[1]["iters"] == 25 and rep_e[1]["gap"] == 0.0
+    assert rep_e[0]["iters"] == 75 and rep_e[2]["iters"] == 75
+    got = stop.cpu().numpy()
+    assert np.all(got[1] == 0.0)
+    assert np.array_equal(got[0], straight.cpu().numpy()[0]) and np.array_equal(got[2], straight.cpu().numpy()[2])
