@@ -138,7 +138,8 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
 void gen_destroy(GenSolver* gs);
 cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                         float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
-                        double sigma, int n_iter, cudaStream_t st, int resume, const int* active);
+                        double sigma, int n_iter, cudaStream_t st, int resume, const int* active,
+                        const float* inv_den_slice);
 cudaError_t gen_report(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                        const float* chi, const float* p, const float* qx, const float* qy, int S, double lambda,
                        int iters, pcs_slice_report* rep, cudaStream_t st);
@@ -261,10 +262,10 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     if (!aligned16(field) || !aligned16(mask) || !aligned16(chi_out) || !aligned16(weight))
         return fail(PCS_EINVAL, "device buffers must be 16-byte aligned");
     if (ctx->gen) {
-        if (inv_den_slice || entry) return fail(PCS_EUNSUPPORTED, "per-slice lambdas need a compiled size");
+        if (entry) return fail(PCS_EUNSUPPORTED, "a compiled variant was asked for an any-size context");
         PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
         PCS_CUDA(pcs::gen_enqueue(ctx->gen, field, mask, weight, chi_out, ctx->chibar, ctx->p, ctx->qx, ctx->qy, S,
-                                  lambda, tau, sigma, n_iter, ctx->stream, resume, active),
+                                  lambda, tau, sigma, n_iter, ctx->stream, resume, active, inv_den_slice),
                  "launch of the any-size kernels");
         ctx->last_iters = n_iter;
         return PCS_OK;
@@ -948,7 +949,8 @@ pcs_status pcs_batch_solve(pcs_batch* b, const pcs_volume* vols, int n_vols, int
         if (V.S == 0) continue;
         if (!V.field || !V.mask || !V.chi_out) return fail(PCS_EINVAL, "volume %d: NULL buffer", v);
         if (!(V.lambda > 0.0) || !std::isfinite(V.lambda)) return fail(PCS_EINVAL, "volume %d: lambda must be > 0", v);
-        if (!find_entry(V.H, V.W, 0)) return fail(PCS_EUNSUPPORTED, "volume %d: no kernel for %d x %d", v, V.H, V.W);
+        if (!find_entry(V.H, V.W, 0) && !pcs::gen_supported(V.H, V.W))
+            return fail(PCS_EUNSUPPORTED, "volume %d: no kernel for %d x %d", v, V.H, V.W);
         int k = -1;
         for (size_t c = 0; c < b->classes.size(); ++c)
             if (b->classes[c].H == V.H && b->classes[c].W == V.W) k = (int)c;

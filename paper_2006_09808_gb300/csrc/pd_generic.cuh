@@ -51,6 +51,7 @@ struct GenParams {
     int phase;             // 0: dual step, 1: primal step
     int store;             // 1: forward transforms of the phase's output to the spectrum
     const int* active;     // NULL, or per-slice flags: 0 = frozen (the row kernel leaves it alone)
+    const float* inv_den_slice;  // NULL, or per-slice 1 / (1 + sigma / lambda_s) (batches)
 };
 
 __device__ __forceinline__ float2 gcmul(float2 a, float2 b) {
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
     if (g.phase == 0) {
         // dual step at both rows (Sec. II.A): p and q from u = D chibar and chibar's differences
         const bool down1 = (i1 + 1 < H);
-        const float inv_den = g.inv_den;
+        const float inv_den = g.inv_den_slice ? __ldg(g.inv_den_slice + s) : g.inv_den;
 #pragma unroll 3
         for (int n = lane; n < W; n += 32) {
             const float2 uv = u[n];

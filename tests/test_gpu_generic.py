@@ -293,3 +293,39 @@ def test_generic_monitored_resume_and_early_stop():
     got = stop.cpu().numpy()
     assert np.all(got[1] == 0.0)
     assert np.array_equal(got[0], straight.cpu().numpy()[0]) and np.array_equal(got[2], straight.cpu().numpy()[2])
+
+
+def test_generic_sizes_in_an_uneven_batch():
+    """An uneven batch mixing the paper's 256 x 258 and 128 x 132 slices (two lambdas in one size
+    class) with a compiled 128 x 128 volume: every slice against the oracle with the class's
+    tau = sigma = 1/L; a volume alone equal bit for bit to the same volume inside the mix."""
+    specs = [(128, 132, 3, 1.0, 91), (256, 258, 2, 0.5, 92), (128, 128, 2, 1.0, 93), (128, 132, 2, 0.25, 94)]
+    probs = [phantoms.volume(H, W, S, seed=sd, lam=lam, n_iter=60) for H, W, S, lam, sd in specs]
+
+    def run(pbs):
+        batch = pcs.pcs_batch_create(autotune=False)
+        vols, outs = [], []
+        for pb in pbs:
+            f = torch.from_numpy(np.array(pb.field, dtype=np.float32)).cuda()
+            m = torch.from_numpy(np.array(pb.mask, dtype=np.uint8)).cuda()
+            chi = torch.full_like(f, float("nan"))
+            vols.append((f, m, pb.lam, chi))
+            outs.append(chi)
+        try:
+            pcs.pcs_batch_solve(batch, vols, 60)
+            torch.cuda.synchronize()
+            Ls = {(pb.field.shape[1], pb.field.shape[2]):
+                  pcs.pcs_batch_tuning(batch, pb.field.shape[1], pb.field.shape[2])["L"] for pb in pbs}
+        finally:
+            pcs.pcs_batch_destroy(batch)
+        return [o.cpu().numpy() for o in outs], Ls
+
+    got, Ls = run(probs)
+    for pb, g in zip(probs, got):
+        S, H, W = pb.field.shape
+        L = Ls[(H, W)]
+        assert 2.5 < L <= math.sqrt(4.0 / 9.0 + 8.0)
+        ref = O.pd_solve(pb.field.astype(np.float64), pb.mask, pb.lam, 1.0 / L, 1.0 / L, 60)
+        assert rel_l2(g, ref) <= TOL, (H, W, pb.lam)
+    alone, _ = run([probs[3]])
+    assert np.array_equal(alone[0], got[3])
