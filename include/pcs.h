@@ -366,8 +366,10 @@ PCS_API pcs_status pcs_batch_create(pcs_batch **out, const pcs_options *opt, int
  * Solve every slice of every volume with n_iter iterations of the Sec. II.A
  * iteration (each volume with its own lambda) and write each volume's chi_out.
  * Enqueued on the batch stream; inputs are copied into per-size packed
- * buffers owned by the batch.  Errors: PCS_EINVAL, PCS_EUNSUPPORTED, PCS_ENOMEM,
- * PCS_ECUDA.
+ * buffers owned by the batch.  Slice sizes: the compiled ones and those
+ * pcs_supported_generic accepts (run by the any-size kernels: row and column
+ * launches per iteration instead of one persistent launch; no variants to
+ * autotune).  Errors: PCS_EINVAL, PCS_EUNSUPPORTED, PCS_ENOMEM, PCS_ECUDA.
  */
 PCS_API pcs_status pcs_batch_solve(pcs_batch *b, const pcs_volume *vols, int n_vols, int n_iter);
 
