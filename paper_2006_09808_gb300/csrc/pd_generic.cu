@@ -62,11 +62,13 @@ struct ColEntry {
     int H;
     size_t smem;
     void (*kern)(GenParams);
-    int tile;  // columns per CTA
+    int tile;     // columns per CTA
+    int threads;  // threads per CTA
 };
 template <int H>
 constexpr ColEntry col_entry() {
-    return ColEntry{H, pcs::GeoCol<H>::SMEM_BYTES, &pcs::gen_cols_fft_kernel<H>, pcs::GeoCol<H>::TY};
+    return ColEntry{H, pcs::GeoCol<H>::SMEM_BYTES, &pcs::gen_cols_fft_kernel<H>, pcs::GeoCol<H>::TY,
+                    pcs::GeoCol<H>::NT};
 }
 const ColEntry k_cols[] = {col_entry<64>(),  col_entry<128>(), col_entry<192>(),
                            col_entry<256>(), col_entry<384>(), col_entry<512>()};
@@ -123,7 +125,7 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
         if (c.H == H) ce = &c;
     gs->cols_kern = ce ? ce->kern : gen_cols_kernel;
     gs->col_tile = ce ? ce->tile : kGenColTile;
-    gs->col_threads = ce ? 256 : kGenColTile * 32;
+    gs->col_threads = ce ? ce->threads : kGenColTile * 32;
     gs->srows = rows_smem(W);
     gs->scols = ce ? ce->smem : cols_smem(H);
     gs->max_slices = max_slices;
