@@ -9,10 +9,14 @@
 //                  complex row (a + i b) through a length-W DFT in shared memory
 //                  -> the dual or primal row phase -> forward DFT, split back into
 //                  the two half-spectrum rows
-//   column kernel: one warp per spectrum column; length-H DFT x D(k)/(H W),
-//                  inverse DFT
-// The DFTs are mixed-radix Stockham passes: 2, 3, 4 as butterflies, larger odd
-// primes as a symmetric direct DFT (terms q and r - q paired).
+//   column kernel: length-H transform x D(k)/(H W), inverse: the register FFT of
+//                  fft_core.cuh for H in {64, 128, 192, 256, 384, 512} (pencils
+//                  of lanes, gen_cols_fft_kernel), else one warp per spectrum
+//                  column with the shared-memory DFT (gen_cols_kernel)
+// The shared-memory DFTs are mixed-radix Stockham passes: 2, 3, 4 as butterflies,
+// larger odd primes as a symmetric direct DFT (terms q and r - q paired).
+// Also here: the FP64 report kernel and the power iteration for ||K||, which reuse
+// the row transforms and the column pass.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,8 +26,8 @@
 namespace pcs {
 
 constexpr int kGenMaxStages = 12;
-constexpr int kGenRowWarps = 8;   // row pairs per CTA of the row kernel
-constexpr int kGenColTile = 16;   // spectrum columns per CTA of the column kernel
+constexpr int kGenRowWarps = 8;   // row pairs per CTA of the row, report and power-iteration kernels
+constexpr int kGenColTile = 16;   // spectrum columns per CTA of the shared-memory column kernel
 
 struct GenPlan {
     int n;                  // transform length
