@@ -56,7 +56,8 @@ typedef struct pcs_ctx pcs_ctx; /* opaque */
 typedef enum pcs_status {
     PCS_OK = 0,
     PCS_EINVAL = 1,       /* bad argument: NULL pointer, non-positive lambda/tau/sigma, S > max_slices ... */
-    PCS_EUNSUPPORTED = 2, /* slice size without a compiled kernel (see pcs_supported_size) */
+    PCS_EUNSUPPORTED = 2, /* slice size or feature without a kernel (see pcs_supported_size,
+                             pcs_supported_generic, pcs_supported_volume_3d) */
     PCS_ENOMEM = 3,       /* device allocation failed */
     PCS_ECUDA = 4,        /* a CUDA runtime call failed (no device, launch failure, ...) */
     PCS_ETIMEOUT = 5,     /* a bounded device wait expired (the balanced schedule's; see pcs_check) */
