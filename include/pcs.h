@@ -420,7 +420,9 @@ PCS_API pcs_status pcs_serve_prepare_size(pcs_server *sv, int H, int W, pcs_tuni
  * Open a request for a volume of S slices of H x W with regularisation lambda.
  * chi_host: host [S][H][W] float32 that receives chi (keep it alive until the
  * request completes).  Returns its id.  PCS_ENOMEM if the volume alone exceeds
- * the budget, PCS_EUNSUPPORTED for a size without a kernel.
+ * the budget, PCS_EUNSUPPORTED for a size neither compiled nor accepted by
+ * pcs_supported_generic (those run the any-size kernels, each slot with its own
+ * half-spectrum scratch, counted in the budget).
  */
 PCS_API pcs_status pcs_serve_open(pcs_server *sv, int H, int W, int S, double lambda, float *chi_host,
                                   long long *id);

@@ -139,7 +139,7 @@ void gen_destroy(GenSolver* gs);
 cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                         float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
                         double sigma, int n_iter, cudaStream_t st, int resume, const int* active,
-                        const float* inv_den_slice);
+                        const float* inv_den_slice, float2* spec);
 cudaError_t gen_report(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                        const float* chi, const float* p, const float* qx, const float* qy, int S, double lambda,
                        int iters, pcs_slice_report* rep, cudaStream_t st);
@@ -265,7 +265,8 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
         if (entry) return fail(PCS_EUNSUPPORTED, "a compiled variant was asked for an any-size context");
         PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
         PCS_CUDA(pcs::gen_enqueue(ctx->gen, field, mask, weight, chi_out, ctx->chibar, ctx->p, ctx->qx, ctx->qy, S,
-                                  lambda, tau, sigma, n_iter, ctx->stream, resume, active, inv_den_slice),
+                                  lambda, tau, sigma, n_iter, ctx->stream, resume, active, inv_den_slice,
+                                  nullptr),
                  "launch of the any-size kernels");
         ctx->last_iters = n_iter;
         return PCS_OK;

@@ -38,6 +38,15 @@ namespace pcs {
 void build_dipole_tables(int H, int W, int b0_axis, std::vector<float>& dtab, std::vector<float>& ddtab);
 void build_twiddles(int n, std::vector<float2>& tw);
 pcs_status set_last_error(pcs_status st, const char* msg);
+// any-size slices (pd_generic.cu)
+struct GenSolver;
+bool gen_supported(int H, int W);
+cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axis, int tv);
+void gen_destroy(GenSolver* gs);
+cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
+                        float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
+                        double sigma, int n_iter, cudaStream_t st, int resume, const int* active,
+                        const float* inv_den_slice, float2* spec);
 }  // namespace pcs
 
 namespace {
@@ -62,10 +71,20 @@ const pcs::KernelEntry* registry_find(int H, int W, int C, int kernel, int threa
     return nullptr;
 }
 
+// Slice sizes the loop serves: a compiled variant, or the any-size kernels.
+bool served_size(int H, int W) { return registry_find(H, W, 0, 0, 0) != nullptr || pcs::gen_supported(H, W); }
+
+// Half-spectrum bytes per voxel of a size run by the any-size kernels (0 for compiled sizes).
+size_t spec_bytes(int H, int W, size_t voxels) {
+    if (registry_find(H, W, 0, 0, 0)) return 0;
+    return voxels / (size_t)W * (size_t)(W / 2 + 1) * sizeof(float2);
+}
+
 // Per slice size: kernel variant, tables and step size, shared by all slots.
 struct SizeInfo {
     int H = 0, W = 0;
     const pcs::KernelEntry* entry = nullptr;
+    pcs::GenSolver* gen = nullptr;  // any-size kernels (tables only; each slot holds its spectrum)
     int max_clusters = 1;
     double L = 0.0;
     float* dtab = nullptr;
@@ -106,7 +125,8 @@ struct Slot {
     unsigned char* mask = nullptr;
     float* chi = nullptr;
     float* state = nullptr;  // chibar, p, qx, qy
-    size_t cap_voxels = 0;
+    float2* spec = nullptr;  // half spectrum, for sizes run by the any-size kernels
+    size_t cap_voxels = 0, cap_spec = 0;
 };
 
 }  // namespace
@@ -185,6 +205,13 @@ pcs_status size_setup(pcs_server* sv, int H, int W, SizeInfo** out) {
     if (st != PCS_OK) return st;
     si.L = si.tuning.L;
     si.entry = registry_find(H, W, si.tuning.cluster_size, si.tuning.kernel, si.tuning.threads);
+    if (!si.entry && pcs::gen_supported(H, W)) {
+        if (!(si.L > 0.0) || pcs::gen_create(&si.gen, H, W, 1, sv->cfg.b0_axis, 0) != cudaSuccess)
+            return pcs::set_last_error(PCS_ECUDA, "serve: any-size set-up");
+        auto res = sv->sizes.emplace(key, si);
+        *out = &res.first->second;
+        return PCS_OK;
+    }
     if (!si.entry || !(si.L > 0.0)) return pcs::set_last_error(PCS_ECUDA, "serve: size set-up");
     int aux = 0;
     if (si.entry->prepare(&si.max_clusters, &aux) != cudaSuccess) return pcs::set_last_error(PCS_ECUDA, "serve: prepare");
@@ -204,14 +231,16 @@ pcs_status size_setup(pcs_server* sv, int H, int W, SizeInfo** out) {
 }
 
 void slot_release(Slot& sl) {
-    void* p[] = {sl.field, sl.mask, sl.chi, sl.state};
+    void* p[] = {sl.field, sl.mask, sl.chi, sl.state, sl.spec};
     for (void* q : p)
         if (q) cudaFree(q);
     sl.field = nullptr;
     sl.mask = nullptr;
     sl.chi = nullptr;
     sl.state = nullptr;
+    sl.spec = nullptr;
     sl.cap_voxels = 0;
+    sl.cap_spec = 0;
 }
 
 // Admit waiting requests (arrival order) while a slot and budget are free.
@@ -234,14 +263,17 @@ void admit(pcs_server* sv) {
         if (sv->bytes_in_use + r.bytes > sv->cfg.hbm_budget_bytes) return;  // wait for memory
         Slot& sl = sv->slots[free_slot];
         const size_t vox = (size_t)r.S * r.H * r.W;
-        if (sl.cap_voxels < vox) {
+        const size_t sb = spec_bytes(r.H, r.W, vox);
+        if (sl.cap_voxels < vox || sl.cap_spec < sb) {
             slot_release(sl);
             if (cudaMalloc(&sl.field, vox * 4) != cudaSuccess || cudaMalloc(&sl.mask, vox) != cudaSuccess ||
-                cudaMalloc(&sl.chi, vox * 4) != cudaSuccess || cudaMalloc(&sl.state, 4 * vox * 4) != cudaSuccess) {
+                cudaMalloc(&sl.chi, vox * 4) != cudaSuccess || cudaMalloc(&sl.state, 4 * vox * 4) != cudaSuccess ||
+                (sb > 0 && cudaMalloc(&sl.spec, sb) != cudaSuccess)) {
                 slot_release(sl);
                 return;  // device memory exhausted beyond the budget: retry later
             }
             sl.cap_voxels = vox;
+            sl.cap_spec = sb;
         }
         sl.req = id;
         r.slot = free_slot;
@@ -275,6 +307,17 @@ bool launch_arrived(pcs_server* sv) {
             cudaError_t e1 =
                 cudaMemcpyAsync(sl.field + a.s0 * slice, a.field, a.n * slice * 4, cudaMemcpyHostToDevice, sl.stream);
             cudaError_t e2 = cudaMemcpyAsync(sl.mask + a.s0 * slice, a.mask, a.n * slice, cudaMemcpyHostToDevice, sl.stream);
+            cudaError_t e3 = cudaSuccess;
+            if (si->gen) {
+                // any-size kernels on this slot's stream and spectrum
+                const double step = 1.0 / si->L;
+                const size_t sp_slice = (size_t)r.H * (r.W / 2 + 1);
+                e3 = pcs::gen_enqueue(si->gen, sl.field + a.s0 * slice, sl.mask + a.s0 * slice, nullptr,
+                                      sl.chi + a.s0 * slice, sl.state + a.s0 * slice, sl.state + vox + a.s0 * slice,
+                                      sl.state + 2 * vox + a.s0 * slice, sl.state + 3 * vox + a.s0 * slice, a.n,
+                                      r.lambda, step, step, sv->cfg.n_iter, sl.stream, 0, nullptr, nullptr,
+                                      sl.spec + a.s0 * sp_slice);
+            }
             pcs::PDParams prm;
             std::memset(&prm, 0, sizeof(prm));
             prm.field = sl.field + a.s0 * slice;
@@ -294,7 +337,7 @@ bool launch_arrived(pcs_server* sv) {
             prm.inv_den = (float)(1.0 / (1.0 + (1.0 / si->L) / r.lambda));
             prm.inv_den_slice = nullptr;
             int ncl = std::min(si->max_clusters, a.n);
-            cudaError_t e3 = si->entry->launch(prm, ncl < 1 ? 1 : ncl, sl.stream);
+            if (!si->gen) e3 = si->entry->launch(prm, ncl < 1 ? 1 : ncl, sl.stream);
             cudaError_t e4 = cudaMemcpyAsync(r.chi_host + a.s0 * slice, sl.chi + a.s0 * slice, a.n * slice * 4,
                                              cudaMemcpyDeviceToHost, sl.stream);
             if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
@@ -388,7 +431,7 @@ pcs_status pcs_serve_start(pcs_server** out, const pcs_server_config* cfg) {
 
 pcs_status pcs_serve_prepare_size(pcs_server* sv, int H, int W, pcs_tuning* info) {
     if (!sv) return pcs::set_last_error(PCS_EINVAL, "server is NULL");
-    if (!registry_find(H, W, 0, 0, 0)) return pcs::set_last_error(PCS_EUNSUPPORTED, "unsupported slice size");
+    if (!served_size(H, W)) return pcs::set_last_error(PCS_EUNSUPPORTED, "unsupported slice size");
     std::lock_guard<std::mutex> lk(sv->mu);
     SizeInfo* si = nullptr;
     pcs_status st = size_setup(sv, H, W, &si);
@@ -399,8 +442,8 @@ pcs_status pcs_serve_prepare_size(pcs_server* sv, int H, int W, pcs_tuning* info
 pcs_status pcs_serve_open(pcs_server* sv, int H, int W, int S, double lambda, float* chi_host, long long* id) {
     if (!sv || !chi_host || !id) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_open: NULL argument");
     if (S < 1 || !(lambda > 0.0)) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_open: S >= 1 and lambda > 0");
-    if (!registry_find(H, W, 0, 0, 0)) return pcs::set_last_error(PCS_EUNSUPPORTED, "pcs_serve_open: unsupported slice size");
-    const size_t bytes = (size_t)S * H * W * kBytesPerVoxel;
+    if (!served_size(H, W)) return pcs::set_last_error(PCS_EUNSUPPORTED, "pcs_serve_open: unsupported slice size");
+    const size_t bytes = (size_t)S * H * W * kBytesPerVoxel + spec_bytes(H, W, (size_t)S * H * W);
     if (bytes > sv->cfg.hbm_budget_bytes) return pcs::set_last_error(PCS_ENOMEM, "pcs_serve_open: volume exceeds the budget");
     std::lock_guard<std::mutex> lk(sv->mu);
     Request r;
@@ -491,6 +534,7 @@ void pcs_serve_stop(pcs_server* sv) {
         cudaFree(kv.second.dtab);
         cudaFree(kv.second.ddtab);
         cudaFree(kv.second.twid);
+        pcs::gen_destroy(kv.second.gen);
     }
     delete sv;
 }

@@ -166,13 +166,15 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
 // Enqueue a solve of S <= max_slices slices on st: zero state, chi and spectrum (or, with
 // resume, continue from the stored chi, chibar, p, q: the spectrum D F chibar is rebuilt),
 // then n_iter iterations of four launches; slices with active[s] = 0 stay as they are;
-// inv_den_slice (optional) gives each slice its own lambda.
+// inv_den_slice (optional) gives each slice its own lambda; spec (optional) replaces the
+// solver's spectrum scratch ([S][H][W/2 + 1] complex).
 // Asynchronous; no allocation.
 cudaError_t gen_enqueue(GenSolver* gs, const float* field, const unsigned char* mask, const float* weight,
                         float* chi, float* chibar, float* p, float* qx, float* qy, int S, double lambda, double tau,
                         double sigma, int n_iter, cudaStream_t st, int resume, const int* active,
-                        const float* inv_den_slice) {
+                        const float* inv_den_slice, float2* spec) {
     GenParams g = gs->g;
+    if (spec) g.spec = spec;  // a caller-owned spectrum (concurrent solves of one size)
     const size_t n = (size_t)S * g.H * g.W;
     cudaError_t e;
     if (!resume &&
@@ -345,7 +347,7 @@ pcs_status pcs_solve_slices_generic(const float* field, const unsigned char* mas
         (e = cudaMalloc(&state, 4 * n * sizeof(float))) != cudaSuccess) {
         ret = failg(PCS_ECUDA, "set-up", e);
     } else if ((e = pcs::gen_enqueue(gs, field, mask, weight, chi_out, state, state + n, state + 2 * n, state + 3 * n,
-                                     S, lambda, tau, sigma, n_iter, st, 0, nullptr, nullptr)) != cudaSuccess) {
+                                     S, lambda, tau, sigma, n_iter, st, 0, nullptr, nullptr, nullptr)) != cudaSuccess) {
         ret = failg(PCS_ECUDA, "launch", e);
     } else if (rep && (e = pcs::gen_report(gs, field, mask, weight, chi_out, state + n, state + 2 * n, state + 3 * n, S,
                                            lambda, n_iter, rep, st)) != cudaSuccess) {

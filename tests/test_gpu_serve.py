@@ -126,8 +126,34 @@ def test_rejections():
         with pytest.raises(pcs.PcsError) as ei:  # 4 x 256 x 256 x 25 B > 1 MiB
             pcs.pcs_serve_open(sv, 256, 256, 4, 1e-3, chi)
         assert ei.value.status == pcs.PCS_ENOMEM
-        with pytest.raises(pcs.PcsError) as ei:
-            pcs.pcs_serve_open(sv, 100, 100, 1, 1e-3, np.zeros((1, 100, 100), np.float32))
+        with pytest.raises(pcs.PcsError) as ei:  # no compiled kernel; 134 = 2 x 67 outside the any-size rule
+            pcs.pcs_serve_open(sv, 100, 134, 1, 1e-3, np.zeros((1, 100, 134), np.float32))
         assert ei.value.status == pcs.PCS_EUNSUPPORTED
     finally:
         pcs.pcs_serve_stop(sv)
+
+
+def test_native_sizes_served_with_the_rest():
+    """Requests of the paper's 128 x 132 and 256 x 258 slices (the any-size kernels, each slot with
+    its own spectrum) served among a compiled 128 x 128 request: mix == alone, and equal to the
+    plain solves with the server's step size, bit for bit."""
+    specs = [(128, 132, 4, 11, 5e-4), (256, 258, 3, 12, 1e-3), (128, 128, 3, 13, 5e-4)]
+    probs = [phantoms.volume(H, W, S, seed=sd, lam=lam, n_iter=N_ITER) for H, W, S, sd, lam in specs]
+    sv = pcs.pcs_serve_start(hbm_budget_bytes=8 << 30, slots=3, n_iter=N_ITER, autotune=False)
+    try:
+        tun = {(H, W): pcs.pcs_serve_prepare_size(sv, H, W) for H, W, *_ in specs}
+        mix, _ = _serve(sv, probs)
+        for k, pb in enumerate(probs):
+            alone, _ = _serve(sv, [pb], chunks=1)
+            assert np.array_equal(mix[k], alone[0]), k
+    finally:
+        pcs.pcs_serve_stop(sv)
+    for k, pb in enumerate(probs[:2]):
+        S, H, W = pb.field.shape
+        L = tun[(H, W)]["L"]
+        f = torch.from_numpy(pb.field).cuda()
+        m = torch.from_numpy(pb.mask).cuda()
+        chi = torch.empty_like(f)
+        pcs.pcs_solve_slices_generic(f, m, pb.lam, 1 / L, 1 / L, N_ITER, chi)
+        torch.cuda.synchronize()
+        assert np.array_equal(mix[k], chi.cpu().numpy()), k
