@@ -132,6 +132,9 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
     std::vector<float2> tw_r, tw_c;
     build_twiddles(W, tw_r);
     build_twiddles(H, tw_c);
+    // the dynamic shared-memory limit is a per-function attribute shared by every size: set it
+    // to what the largest accepted size needs, so that solvers of several sizes coexist
+    const int rows_max = (int)rows_smem(kGenMaxLen), cols_max = (int)cols_smem(kGenMaxLen);
     cudaError_t e;
     if ((e = cudaMalloc(&gs->tabs, (size_t)(W + H) * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&gs->spec, (size_t)max_slices * H * M1 * sizeof(float2))) != cudaSuccess ||
@@ -139,14 +142,14 @@ cudaError_t gen_create(GenSolver** out, int H, int W, int max_slices, int b0_axi
             cudaSuccess ||
         (e = cudaMemcpy(gs->tabs, tw_r.data(), W * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(gs->tabs + W, tw_c.data(), H * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(gen_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->srows)) !=
+        (e = cudaFuncSetAttribute(gen_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_max)) !=
             cudaSuccess ||
-        (e = cudaFuncSetAttribute(gen_report_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->srows)) !=
+        (e = cudaFuncSetAttribute(gen_report_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_max)) !=
             cudaSuccess ||
-        (e = cudaFuncSetAttribute(gen_opnorm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)gs->srows)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(gs->cols_kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gs->scols)) !=
-            cudaSuccess) {
+        (e = cudaFuncSetAttribute(gen_opnorm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_max)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(gs->cols_kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ce ? (int)gs->scols : cols_max)) != cudaSuccess) {  // per-H instances: own size
         gen_destroy(gs);
         return e;
     }

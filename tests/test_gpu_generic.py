@@ -329,3 +329,27 @@ def test_generic_sizes_in_an_uneven_batch():
         assert rel_l2(g, ref) <= TOL, (H, W, pb.lam)
     alone, _ = run([probs[3]])
     assert np.array_equal(alone[0], got[3])
+
+
+def test_solvers_of_several_sizes_coexist():
+    """A larger any-size solver made before a smaller one (and the shared-memory column kernel's
+    H = 90 before H = 30) still launches: the kernels' shared-memory limits do not depend on the
+    order in which sizes are set up."""
+    big = phantoms.volume(256, 258, 1, seed=95, lam=1.0, n_iter=10)
+    small = phantoms.volume(128, 132, 1, seed=96, lam=1.0, n_iter=10)
+    odd_big = phantoms.volume(90, 98, 1, seed=97, lam=1.0, n_iter=10)
+    odd_small = phantoms.volume(30, 42, 1, seed=98, lam=1.0, n_iter=10)
+    ctxs = []
+    try:
+        for pb in (big, odd_big, small, odd_small):  # larger sizes first
+            ctxs.append(pcs.pcs_create(pb.field.shape[1], pb.field.shape[2], 1))
+        for ctx, pb in zip(ctxs, (big, odd_big, small, odd_small)):
+            f = torch.from_numpy(np.array(pb.field, dtype=np.float32)).cuda()
+            m = torch.from_numpy(np.array(pb.mask, dtype=np.uint8)).cuda()
+            chi = torch.empty_like(f)
+            pcs.pcs_solve_slices(ctx, f, m, 1.0, STEP, STEP, 10, chi)
+            torch.cuda.synchronize()
+            assert rel_l2(chi.cpu().numpy(), oracle(pb.field, pb.mask, 1.0, 10)) <= TOL
+    finally:
+        for c in ctxs:
+            pcs.pcs_destroy(c)
