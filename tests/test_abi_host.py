@@ -106,3 +106,22 @@ def test_binding_fails_loudly_without_library(tmp_path):
             mod.load_library(str(tmp_path / "missing.so"))
     finally:
         mod._lib = saved
+
+
+def test_bindings_refuse_host_tensors():
+    """No CPU path: the device entry points reject CPU tensors before anything runs."""
+    torch = pytest.importorskip("torch")
+    f = torch.zeros((2, 128, 132))
+    m = torch.ones((2, 128, 132), dtype=torch.uint8)
+    chi = torch.empty_like(f)
+    calls = [
+        lambda: pcs.pcs_solve_slices_generic(f, m, 1.0, 0.3, 0.3, 5, chi),
+        lambda: pcs.pcs_solve_volume_3d(torch.zeros((32, 64, 64)), torch.ones((32, 64, 64), dtype=torch.uint8),
+                                        1.0, 0.3, 0.3, 5, torch.empty((32, 64, 64))),
+        lambda: pcs.pcs_field_map(torch.zeros((4, 8), dtype=torch.complex64), torch.zeros((4, 8), dtype=torch.complex64),
+                                  0.6e-3, 3.0, 0.1, torch.empty((4, 8)), torch.empty((4, 8)),
+                                  torch.empty((4, 8), dtype=torch.uint8)),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError, match="CUDA device"):
+            call()
