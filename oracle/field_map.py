@@ -15,11 +15,11 @@ outputs but gives no formula; the readings taken here:
   keeps the phase small), and dB in ppm = that angle / (2 pi gamma_bar B0
   T_shift) * 1e6 with gamma_bar = 42.577478518 MHz/T;
 * W = |S0| / max |S0| over the volume (magnitude weighting, values in [0, 1]);
-* Mask: |S0|^2 >= t^2 max |S0|^2 for a relative threshold t.  This decision
-  sets a 0/1 value, so it is taken in float32 with a fixed operation order
-  (re*re + im*im, each product and the sum rounded to float32; the threshold
-  t^2 rounded to float32 once; their product rounded to float32), the same
-  arithmetic the GPU kernel uses.
+* Mask: |S0|^2 >= t^2 max |S0|^2 for a relative threshold t, decided in
+  FP64 from the acquisitions' values (exact squares of float32 inputs up to
+  one FP64 rounding).  A float32 implementation can decide the other way only
+  for voxels whose |S0|^2 lies within float32 rounding of t^2 max |S0|^2;
+  ``mask_boundary_band`` marks those voxels.
 
 The field is set to zero outside the mask.
 """
@@ -38,21 +38,28 @@ def ppm_per_radian(b0_tesla: float, t_shift_s: float) -> float:
     return 1e6 / (2.0 * math.pi * GAMMA_BAR_HZ_PER_T * b0_tesla * t_shift_s)
 
 
-def mag2_f32(s: np.ndarray) -> np.ndarray:
-    """|s|^2 in float32: re*re + im*im, every operation rounded to float32."""
-    re = np.ascontiguousarray(s.real, dtype=np.float32)
-    im = np.ascontiguousarray(s.imag, dtype=np.float32)
-    return (re * re) + (im * im)
+def mag2(s: np.ndarray) -> np.ndarray:
+    """|s|^2 = re^2 + im^2 in FP64."""
+    z = np.asarray(s).astype(np.complex128)
+    return z.real * z.real + z.imag * z.imag
+
+
+def mask_boundary_band(s0: np.ndarray, threshold: float, rel: float = 8 * 2.0**-24) -> np.ndarray:
+    """Voxels whose mask decision is within ``rel`` (relative) of the threshold: |S0|^2 and
+    t^2 max |S0|^2 closer than rel * (|S0|^2 + t^2 max |S0|^2).  Outside this band a float32
+    evaluation (a few roundings of relative size 2^-24 each) decides as the FP64 one does."""
+    m2 = mag2(s0)
+    lim = threshold * threshold * (float(m2.max()) if m2.size else 0.0)
+    return np.abs(m2 - lim) <= rel * (m2 + lim)
 
 
 def field_map(s0: np.ndarray, s1: np.ndarray, t_shift_s: float, b0_tesla: float, threshold: float):
     """(field ppm float64, weight float64, mask uint8) from the two complex acquisitions."""
     s0 = np.asarray(s0)
     s1 = np.asarray(s1)
-    m2 = mag2_f32(s0)
-    max2 = np.float32(m2.max()) if m2.size else np.float32(0)
-    thr2 = np.float32(threshold * threshold)
-    mask = (m2 >= np.float32(thr2 * max2)).astype(np.uint8)
+    m2 = mag2(s0)
+    max2 = float(m2.max()) if m2.size else 0.0
+    mask = (m2 >= threshold * threshold * max2).astype(np.uint8)
     z = s1.astype(np.complex128) * np.conj(s0.astype(np.complex128))
     field = np.angle(z) * ppm_per_radian(b0_tesla, t_shift_s)
     field = np.where(mask != 0, field, 0.0)

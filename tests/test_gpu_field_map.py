@@ -38,6 +38,17 @@ def gpu_map(s0, s1, thr):
     return f.cpu().numpy(), w.cpu().numpy(), m.cpu().numpy()
 
 
+def check_mask(m, rm, s0, thr, max_frac=1e-4):
+    """GPU mask (a float32 decision) against the oracle's FP64 decision: they may differ only at
+    voxels within float32 rounding of the threshold, and those must be few.  Returns the voxels
+    where the two agree."""
+    diff = m != rm
+    band = FM.mask_boundary_band(s0, thr)
+    assert not np.any(diff & ~band), f"{int(np.sum(diff & ~band))} mask voxels differ outside the rounding band"
+    assert diff.sum() <= max(1, max_frac * m.size), int(diff.sum())
+    return ~diff
+
+
 def phase_err(a, b):
     """Difference of two fields as a phase, folded into (-pi, pi]."""
     d = (np.asarray(a, np.float64) - np.asarray(b, np.float64)) / FM.ppm_per_radian(B0, T_SHIFT)
@@ -50,10 +61,10 @@ def test_field_map_parity(H, S, thr):
     s0, s1 = phantoms.echo_pair(pb.field, pb.mask, seed=62)
     f, w, m = gpu_map(s0, s1, thr)
     rf, rw, rm = FM.field_map(s0, s1, T_SHIFT, B0, thr)
-    assert np.array_equal(m, rm)  # the 0/1 decision is taken in the same float32 arithmetic
+    agree = check_mask(m, rm, s0, thr)
     assert 0 < m.sum() < m.size
     assert np.max(np.abs(w - rw)) <= 1e-6
-    assert np.max(phase_err(f, rf)) <= 1e-5
+    assert np.max(phase_err(f, rf)[agree]) <= 1e-5
     assert np.all(f[m == 0] == 0)
 
 
@@ -77,6 +88,8 @@ def test_pipeline_echoes_to_chi_matches_the_oracle_chain():
     s0, s1 = phantoms.echo_pair(pb.field, pb.mask, seed=64)
     f, w, m = gpu_map(s0, s1, 0.3)
     rf, rw, rm = FM.field_map(s0, s1, T_SHIFT, B0, 0.3)
+    check_mask(m, rm, s0, 0.3)
+    assert np.array_equal(m, rm)  # this seeded volume has no voxel in the rounding band: the chains agree
     L = 2.832522691076350  # full-mask ||K|| of 64 x 64 (tests/golden/opnorm_full_mask.txt)
     ref = O.pd_solve(rf, rm, pb.lam, 1 / L, 1 / L, pb.n_iter, weight=rw)
     ft, mt, wt = (torch.from_numpy(a).cuda() for a in (f, m, w))
@@ -114,7 +127,8 @@ def test_field_map_edges_and_errors():
     s1 = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
     f, w, m = gpu_map(s0, s1, 0.4)
     rf, rw, rm = FM.field_map(s0, s1, T_SHIFT, B0, 0.4)
-    assert np.array_equal(m, rm) and np.max(np.abs(w - rw)) <= 1e-6 and np.max(phase_err(f, rf)) <= 1e-5
+    agree = check_mask(m, rm, s0, 0.4)
+    assert np.max(np.abs(w - rw)) <= 1e-6 and np.max(phase_err(f, rf)[agree]) <= 1e-5
     # inputs off their 16-byte alignment are refused
     z1 = torch.ones(17, dtype=torch.complex64, device="cuda")[1:]
     o1 = [torch.empty(16, device="cuda"), torch.empty(16, device="cuda"), torch.empty(16, dtype=torch.uint8, device="cuda")]

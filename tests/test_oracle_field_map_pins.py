@@ -1,6 +1,7 @@
 """Pins of the field-map oracle (``oracle/field_map.py``) to things other than itself."""
 
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -65,11 +66,24 @@ def test_weight_and_mask_invariants():
     assert not m_none.any()
 
 
-def test_mask_decision_in_float32_at_the_boundary():
-    # |s|^2 = 0.25 exactly and max |s|^2 = 1: threshold 0.5 -> t^2 max = 0.25 -> kept (>=)
-    s0 = np.array([[[1.0 + 0j, 0.3 + 0.4j, 0.5 + 0j, 0.49 + 0j]]], dtype=np.complex64)
+def test_mask_decision_at_the_boundary_by_exact_arithmetic():
+    # max |s|^2 = 1 and threshold 0.5: a voxel is kept iff |s|^2 >= 1/4, decided here by exact
+    # rational arithmetic on the float32 inputs.  The last voxel lies 3.7e-9 below 1/4, which a
+    # float32 evaluation rounds up to 1/4 (and keeps): the oracle must decide exactly.
+    re_last = np.float32(0.5 - 2.0**-25)
+    im_last = np.float32(1.653e-4)
+    s0 = np.array([[[1.0 + 0j, 0.3 + 0.4j, 0.5 + 0j, 0.49 + 0j, complex(re_last, im_last)]]], dtype=np.complex64)
+    want = []
+    for z in s0.ravel():
+        m2 = Fraction(float(z.real)) ** 2 + Fraction(float(z.imag)) ** 2
+        want.append(1 if m2 >= Fraction(1, 4) else 0)
+    assert want == [1, 1, 1, 0, 0]
+    f32 = np.float32(re_last) * np.float32(re_last) + np.float32(im_last) * np.float32(im_last)
+    assert f32 == np.float32(0.25)  # the float32 evaluation sits on the threshold
     _, _, m = FM.field_map(s0, s0, 0.6e-3, 3.0, 0.5)
-    assert m.tolist() == [[[1, 1, 1, 0]]]
+    assert m.ravel().tolist() == want
+    band = FM.mask_boundary_band(s0, 0.5)
+    assert band.ravel().tolist() == [False, True, True, False, True]  # 0.3+0.4i: 4.8e-8 above 1/4
 
 
 def test_scaling_both_acquisitions_changes_nothing():
