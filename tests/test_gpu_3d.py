@@ -63,6 +63,19 @@ def test_parity_3d(S, H, n_iter, lam, tv):
         assert rel_l2(got[s], ref[s]) <= 10 * TOL, s
 
 
+def test_parity_3d_at_the_bench_iteration_count():
+    """64 x 64 x 32 after 500 iterations (the bench's count) against the whole-volume oracle:
+    the volume and every slice within 1e-4."""
+    n_iter = 500
+    pb = phantoms.volume(64, 64, 32, seed=54, lam=5e-4, n_iter=n_iter)
+    ref = O3.pd_solve_3d(pb.field.astype(np.float64), pb.mask, pb.lam, STEP, STEP, n_iter)
+    got = gpu3(pb.field, pb.mask, pb.lam, n_iter)
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, ref) <= TOL
+    for s in range(pb.field.shape[0]):
+        assert rel_l2(got[s], ref[s]) <= TOL, s
+
+
 def test_weighted_3d_parity():
     pb = phantoms.volume(64, 64, 32, seed=52, lam=1.0, n_iter=80)
     w = phantoms.magnitude_weight(pb.mask, seed=53)

@@ -48,7 +48,7 @@ def _batch_solve(problems, n_iter, autotune=True, batch=None):
         outs.append(chi)
     try:
         pcs.pcs_batch_solve(batch, vols, n_iter)
-        torch.cuda.synchronize()
+        pcs.pcs_batch_check(batch)  # synchronises; PCS_ETIMEOUT if a schedule wait gave up
         tunings = {pb.field.shape[1]: pcs.pcs_batch_tuning(batch, pb.field.shape[1], pb.field.shape[2])
                    for pb in problems}
     finally:
@@ -123,3 +123,39 @@ def test_uneven_batch_recipe_subset_vs_oracle():
         L = tun[H]["L"]
         ref = O.pd_solve(pb.field[s].astype(np.float64), pb.mask[s], pb.lam, 1.0 / L, 1.0 / L, 400)
         assert rel_l2(g[s], ref) <= TOL, (H, s)
+
+
+def test_uneven_batch_full_recipe_vs_oracle():
+    """All 48 volumes of the uneven-batch recipe (about 2.7e8 voxels, 400 iterations) in one batch
+    call, the bench's launch; one sampled slice of every volume against the FP64 oracle (rel-L2
+    1e-4), the oracle solves spread over the host cores."""
+    import oracle_workers as OW
+
+    specs = phantoms.config4_volumes()
+    with OW.spawn_pool() as ex:
+        data = list(ex.map(OW.gen_volume, specs))
+        batch = pcs.pcs_batch_create(autotune=True)
+        vols, outs = [], []
+        for (f, m), sp in zip(data, specs):
+            ft = torch.from_numpy(f).cuda()
+            mt = torch.from_numpy(m).cuda()
+            chi = torch.full_like(ft, float("nan"))
+            vols.append((ft, mt, sp["lam"], chi))
+            outs.append(chi)
+        try:
+            pcs.pcs_batch_solve(batch, vols, 400)
+            pcs.pcs_batch_check(batch)
+            tun = {n: pcs.pcs_batch_tuning(batch, n, n) for n in {sp["size"] for sp in specs}}
+        finally:
+            pcs.pcs_batch_destroy(batch)
+        rng = np.random.default_rng(48)
+        picks = [int(rng.integers(0, sp["slices"])) for sp in specs]
+        jobs = []
+        for (f, m), sp, s in zip(data, specs, picks):
+            L = tun[sp["size"]]["L"]
+            jobs.append((f[s], m[s], sp["lam"], 1.0 / L, 1.0 / L, 400))
+        refs = list(ex.map(OW.oracle_slice, jobs))
+    for k, (sp, s, ref) in enumerate(zip(specs, picks, refs)):
+        got = outs[k][s].cpu().numpy()
+        assert np.all(np.isfinite(got)), k
+        assert rel_l2(got, ref) <= TOL, (k, sp["size"], s)

@@ -92,6 +92,20 @@ def test_generic_weighted_and_batch_independence():
     assert np.array_equal(alone[0], got[2])
 
 
+def test_generic_stent_shape_at_the_bench_iteration_count():
+    """256 x 258 x 25 solved in the bench's launch (all slices, 500 iterations, lambda 5e-4);
+    three sampled slices against the oracle after the same 500 iterations, each within 1e-4."""
+    n_iter = 500
+    pb = phantoms.volume(256, 258, 25, seed=0, lam=5e-4, n_iter=n_iter, name="bench258")
+    got = gpu_generic(pb.field, pb.mask, pb.lam, n_iter)
+    assert np.all(np.isfinite(got))
+    for s in (0, 12, 24):
+        ref = oracle(pb.field[s], pb.mask[s], pb.lam, n_iter)
+        assert rel_l2(got[s], ref) <= TOL, s
+        m = pb.mask[s].astype(bool)
+        assert rel_l2(got[s][m], ref[m]) <= TOL, s
+
+
 def test_generic_full_stent_shape():
     """256 x 258 x 25, the stent acquisition's shape, 20 iterations against the oracle."""
     pb = phantoms.volume(256, 258, 25, seed=73, lam=5e-4, n_iter=20)

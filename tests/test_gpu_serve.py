@@ -3,7 +3,9 @@
 Requests of different slice sizes are opened and their slices pushed in
 chunks while other requests run; each result must equal (bitwise) the same
 volume served alone, and the plain solve with the server's kernel variant and
-step size.  Admission respects the memory budget.
+step size, and a sampled slice of every served request must match the FP64
+oracle after the same iterations at the server's step size (rel-L2 1e-4).
+Admission respects the memory budget.
 """
 
 import time
@@ -15,9 +17,20 @@ torch = pytest.importorskip("torch")
 
 import paper_2006_09808_gb300 as pcs  # noqa: E402
 import phantoms  # noqa: E402
+from oracle import pd_oracle as O  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 N_ITER = 80
+TOL = 1e-4  # relative L2 on chi against the FP64 oracle
+
+
+def check_against_oracle(served, pb, L, k):
+    """The middle slice of a served request against the oracle at the server's tau = sigma = 1/L."""
+    s = pb.field.shape[0] // 2
+    ref = O.pd_solve(pb.field[s].astype(np.float64), pb.mask[s], pb.lam, 1 / L, 1 / L, N_ITER)
+    got = served[s].astype(np.float64)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel <= TOL, (k, rel)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -92,6 +105,8 @@ def test_mix_equals_alone_and_plain():
     finally:
         pcs.pcs_serve_stop(sv)
     for k, pb in enumerate(probs):
+        check_against_oracle(mix[k], pb, tun[pb.field.shape[1]]["L"], k)
+    for k, pb in enumerate(probs):
         S, H, W = pb.field.shape
         t = tun[H]
         f = torch.from_numpy(pb.field).cuda()
@@ -148,6 +163,9 @@ def test_native_sizes_served_with_the_rest():
             assert np.array_equal(mix[k], alone[0]), k
     finally:
         pcs.pcs_serve_stop(sv)
+    for k, pb in enumerate(probs):
+        S, H, W = pb.field.shape
+        check_against_oracle(mix[k], pb, tun[(H, W)]["L"], k)
     for k, pb in enumerate(probs[:2]):
         S, H, W = pb.field.shape
         L = tun[(H, W)]["L"]
