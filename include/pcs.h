@@ -176,7 +176,9 @@ PCS_API pcs_status pcs_solve_slices_weighted(pcs_ctx *ctx, const float *field, c
  *
  * pcs_check: synchronise the context's stream and return PCS_ETIMEOUT if any
  * earlier solve on it gave up a wait (clearing the report), else PCS_OK
- * (PCS_ECUDA if the stream reports a CUDA error).
+ * (PCS_ECUDA if the stream reports a CUDA error).  The entry points that
+ * synchronise the stream themselves (pcs_solve_slices_host, and the solves
+ * given a report array) make the same check and return PCS_ETIMEOUT.
  */
 PCS_API pcs_status pcs_check(pcs_ctx *ctx);
 
@@ -377,6 +379,13 @@ PCS_API pcs_status pcs_batch_solve(pcs_batch *b, const pcs_volume *vols, int n_v
 /* The tuning record of slice size H x W (PCS_EINVAL if that size was never solved). */
 PCS_API pcs_status pcs_batch_tuning(pcs_batch *b, int H, int W, pcs_tuning *out);
 
+/*
+ * Synchronise the batch stream and return PCS_ETIMEOUT if a launch of any size
+ * class gave up a bounded wait of the balanced schedule (that call's results
+ * are invalid; see pcs_check), else PCS_OK.  Clears the reports.
+ */
+PCS_API pcs_status pcs_batch_check(pcs_batch *b);
+
 /* Release the batch solver. NULL-safe. */
 PCS_API void pcs_batch_destroy(pcs_batch *b);
 
@@ -457,10 +466,13 @@ PCS_API void pcs_serve_stop(pcs_server *sv);
  * size that every GPU loading libpcs holds until process exit (~16.5 MiB):
  * S*H*W may not exceed PCS_NOALLOC_MAX_VOXELS; larger calls fail with
  * PCS_EINVAL and a message.  The first call on a device sets that device up
- * (looks up the arrays' addresses, sets kernel attributes): make it before
- * any stream capture.  All calls share the arrays and each leaves its state
- * in them; calls that overlap on the GPU race and must be serialised by the
- * caller.  Calls no allocating CUDA or library routine.
+ * (looks up the arrays' addresses, sets kernel attributes), and the first
+ * call of each slice size and b0_axis uploads that size's kernel tables into
+ * its own fixed region (waiting for the upload on the stream); a region is
+ * never rewritten.  Make those first calls before any stream capture.  All
+ * calls share the state arrays and each leaves its state in them; calls that
+ * overlap on the GPU race and must be serialised by the caller.  Calls no
+ * allocating CUDA or library routine.
  */
 #define PCS_NOALLOC_MAX_VOXELS 1048576
 PCS_API pcs_status pcs_solve_slices_noalloc(const float *field, const unsigned char *mask, int H, int W,

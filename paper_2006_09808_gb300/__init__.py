@@ -170,6 +170,7 @@ def load_library(path: str = LIB_PATH):
         "pcs_batch_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(pcs_options), i, vp]),
         "pcs_batch_solve": (i, [vp, ctypes.POINTER(pcs_volume), i, i]),
         "pcs_batch_tuning": (i, [vp, i, i, ctypes.POINTER(pcs_tuning)]),
+        "pcs_batch_check": (i, [vp]),
         "pcs_batch_destroy": (None, [vp]),
         "pcs_serve_start": (i, [ctypes.POINTER(vp), ctypes.POINTER(pcs_server_config)]),
         "pcs_serve_prepare_size": (i, [vp, i, i, ctypes.POINTER(pcs_tuning)]),
@@ -495,6 +496,11 @@ def pcs_batch_tuning(batch, H: int, W: int):
     t = pcs_tuning()
     _check(load_library().pcs_batch_tuning(batch, H, W, ctypes.byref(t)), "pcs_batch_tuning")
     return t.as_dict()
+
+
+def pcs_batch_check(batch):
+    """Synchronise the batch stream; raise PcsError(PCS_ETIMEOUT) if a launch gave up a bounded wait."""
+    _check(load_library().pcs_batch_check(batch), "pcs_batch_check")
 
 
 def pcs_batch_destroy(batch):

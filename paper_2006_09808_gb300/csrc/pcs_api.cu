@@ -371,6 +371,19 @@ pcs_status launch_solve(pcs_ctx* ctx, const float* field, const unsigned char* m
     return PCS_OK;
 }
 
+// The context's error word, read after the work on its stream: set when a bounded wait of
+// the balanced schedule gave up, which makes that solve's results invalid.  Clears the word.
+pcs_status check_err_word(pcs_ctx* ctx) {
+    int flag = 0;
+    PCS_CUDA(cudaMemcpyAsync(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "D2H error word");
+    PCS_CUDA(cudaStreamSynchronize(ctx->stream), "stream sync");
+    if (flag) {
+        PCS_CUDA(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream), "clear error word");
+        return fail(PCS_ETIMEOUT, "a solve on this context gave up waiting for another cluster (its results are invalid)");
+    }
+    return PCS_OK;
+}
+
 // Bounded wait of the balanced schedule on a flag nothing sets.
 __global__ void wait_selftest_kernel(const int* flag, long long limit, int* out) {
     if (threadIdx.x == 0) out[0] = pcs::wait_flag(flag, limit) ? 0 : 1;
@@ -592,14 +605,7 @@ pcs_status pcs_schedule_plan(int S, int n_iter, int clusters, int* segments, int
 pcs_status pcs_check(pcs_ctx* ctx) {
     if (!ctx) return fail(PCS_EINVAL, "ctx is NULL");
     PCS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    int flag = 0;
-    PCS_CUDA(cudaMemcpyAsync(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "D2H error word");
-    PCS_CUDA(cudaStreamSynchronize(ctx->stream), "stream sync");
-    if (flag) {
-        PCS_CUDA(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream), "clear error word");
-        return fail(PCS_ETIMEOUT, "a solve on this context gave up waiting for another cluster (its results are invalid)");
-    }
-    return PCS_OK;
+    return check_err_word(ctx);
 }
 
 pcs_status pcs_selftest_wait(void* cuda_stream, long long limit_cycles, int* gave_up) {
@@ -635,7 +641,8 @@ pcs_status pcs_solve_slices(pcs_ctx* ctx, const float* field, const unsigned cha
     if (!lk.owns_lock()) return fail(PCS_EBUSY, "context in use by another thread");
     st = launch_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out);
     if (st != PCS_OK || !rep) return st;
-    return pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, rep, nullptr);
+    st = pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, rep, nullptr);  // synchronises the stream
+    return st != PCS_OK ? st : check_err_word(ctx);
 }
 
 pcs_status pcs_solve_slices_weighted(pcs_ctx* ctx, const float* field, const unsigned char* mask,
@@ -652,7 +659,8 @@ pcs_status pcs_solve_slices_weighted(pcs_ctx* ctx, const float* field, const uns
     st = launch_solve(ctx, field, mask, S, lambda, tau, sigma, n_iter, chi_out, nullptr, nullptr, 0, 0, nullptr,
                       weight);
     if (st != PCS_OK || !rep) return st;
-    return pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, rep, weight);
+    st = pcs::ctx_report(ctx, field, mask, S, lambda, chi_out, rep, weight);  // synchronises the stream
+    return st != PCS_OK ? st : check_err_word(ctx);
 }
 
 pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const unsigned char* mask_host, int S,
@@ -678,7 +686,8 @@ pcs_status pcs_solve_slices_host(pcs_ctx* ctx, const float* field_host, const un
     if (st != PCS_OK) return st;
     PCS_CUDA(cudaMemcpyAsync(chi_out_host, ctx->st_chi, m * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
              "D2H chi");
-    PCS_CUDA(cudaStreamSynchronize(ctx->stream), "stream sync");
+    st = check_err_word(ctx);  // synchronises the stream
+    if (st != PCS_OK) return st;
     if (rep) return pcs::ctx_report(ctx, ctx->st_field, ctx->st_mask, S, lambda, ctx->st_chi, rep, nullptr);
     return PCS_OK;
 }
@@ -1026,6 +1035,21 @@ pcs_status pcs_batch_tuning(pcs_batch* b, int H, int W, pcs_tuning* out) {
             return PCS_OK;
         }
     return fail(PCS_EINVAL, "size %d x %d not solved by this batch", H, W);
+}
+
+pcs_status pcs_batch_check(pcs_batch* b) {
+    if (!b) return fail(PCS_EINVAL, "batch is NULL");
+    std::unique_lock<std::mutex> lk(b->mu, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(PCS_EBUSY, "batch in use by another thread");
+    PCS_CUDA(cudaSetDevice(b->device), "cudaSetDevice");
+    PCS_CUDA(cudaStreamSynchronize(b->stream), "stream sync");
+    pcs_status ret = PCS_OK;
+    for (auto& c : b->classes) {
+        if (!c.ctx) continue;
+        pcs_status st = check_err_word(c.ctx);  // every size class: read (and clear) its word
+        if (ret == PCS_OK) ret = st;
+    }
+    return ret;
 }
 
 void pcs_batch_destroy(pcs_batch* b) {

@@ -14,13 +14,18 @@
 //
 // Per-device set-up happens on the first call on each device (with that
 // device current): the arrays' device addresses are looked up with
-// cudaGetSymbolAddress and the kernel attributes are set.  Make that first
-// call before any stream capture.
+// cudaGetSymbolAddress and the kernel attributes are set.  Each compiled
+// slice size and B0 axis has its own fixed region of the table arrays,
+// uploaded by the first call of that size and axis on the device (that call
+// waits for the upload on its stream) and never rewritten, so a call of one
+// size can never read another size's tables.  Make the first call of every
+// size and axis before any stream capture.
 //
-// All calls share the same arrays and each call leaves its state behind; the
-// kernel zeroes the state of every slice before iterating, so nothing needs
-// clearing between calls.  Calls that overlap on the GPU (from two streams or
-// two threads) race on these arrays and must be serialised by the caller.
+// All calls share the state arrays and each call leaves its state behind;
+// the kernel zeroes the state of every slice before iterating, so nothing
+// needs clearing between calls.  Calls that overlap on the GPU (from two
+// streams or two threads) race on the state arrays and must be serialised
+// by the caller.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -42,14 +47,38 @@ pcs_status set_last_error(pcs_status st, const char* msg);
 namespace {
 
 constexpr size_t kMaxVoxels = PCS_NOALLOC_MAX_VOXELS;  // S * H * W per call
-constexpr int kMaxSide = 512;
+
+// The compiled slice sizes (square) and their table regions: dtab [n/2][n] and ddtab [n] per
+// (size, B0 axis), twiddles [n] per size.
+constexpr int kSizes[] = {64, 128, 192, 256, 384, 512};
+constexpr int kNumSizes = 6;
+constexpr size_t dtab_offset(int k, int b0) {
+    size_t o = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < kNumSizes; ++j) {
+            if (a == b0 && j == k) return o;
+            o += (size_t)(kSizes[j] / 2) * kSizes[j];
+        }
+    return o;
+}
+constexpr size_t line_offset(int k, int b0) {  // ddtab per (size, axis); twiddles use b0 = 0
+    size_t o = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < kNumSizes; ++j) {
+            if (a == b0 && j == k) return o;
+            o += (size_t)kSizes[j];
+        }
+    return o;
+}
+constexpr size_t kDtabFloats = dtab_offset(kNumSizes, 1);  // past the last region: the total
+constexpr size_t kLineFloats = line_offset(kNumSizes, 1);
 
 // scratch state: chibar, p, qx, qy, kMaxVoxels floats each
 static __device__ __align__(256) float g_noalloc_state[4 * kMaxVoxels];
-// dipole table [W/2][H], packed-column table [H], twiddles [max(H, W)]
-static __device__ __align__(256) float g_noalloc_dtab[(kMaxSide / 2) * kMaxSide];
-static __device__ __align__(256) float g_noalloc_ddtab[kMaxSide];
-static __device__ __align__(256) float2 g_noalloc_twid[kMaxSide];
+// D tables of every (size, axis) region (about 2 MB), packed-column tables, twiddles
+static __device__ __align__(256) float g_noalloc_dtab[kDtabFloats];
+static __device__ __align__(256) float g_noalloc_ddtab[kLineFloats];
+static __device__ __align__(256) float2 g_noalloc_twid[kLineFloats / 2];  // sum of the sizes
 
 struct DeviceSetup {
     bool ready = false;
@@ -57,7 +86,8 @@ struct DeviceSetup {
     float* dtab = nullptr;
     float* ddtab = nullptr;
     float2* twid = nullptr;
-    int tab_H = 0, tab_W = 0, tab_b0 = -1;  // tables currently uploaded
+    bool tables[kNumSizes][2] = {};   // (size, axis) region uploaded
+    bool twiddles[kNumSizes] = {};    // size's twiddle region uploaded
     const pcs::KernelEntry* prepared[16] = {};
     int max_clusters[16] = {};
 };
@@ -143,23 +173,35 @@ extern "C" pcs_status pcs_solve_slices_noalloc(const float* field, const unsigne
         if ((e = entry->prepare(&d.max_clusters[slot], &a)) != cudaSuccess) return err(PCS_ECUDA, "kernel attributes", e);
         d.prepared[slot] = entry;
     }
-    if (d.tab_H != H || d.tab_W != W || d.tab_b0 != b0_axis) {
+    int k_size = -1;
+    for (int k = 0; k < kNumSizes; ++k)
+        if (kSizes[k] == H && H == W) k_size = k;
+    if (k_size < 0) return pcs::set_last_error(PCS_EUNSUPPORTED, "pcs_solve_slices_noalloc: no table region");
+    float* dtab_r = d.dtab + dtab_offset(k_size, b0_axis);
+    float* ddtab_r = d.ddtab + line_offset(k_size, b0_axis);
+    float2* twid_r = d.twid + line_offset(k_size, 0);  // float2 entries: the sizes before this one
+    if (!d.tables[k_size][b0_axis] || !d.twiddles[k_size]) {
+        // first call of this size (or axis) on this device: fill the regions not yet filled, once
         std::vector<float> dtab, ddtab;
         std::vector<float2> tw;
         pcs::build_dipole_tables(H, W, b0_axis, dtab, ddtab);
-        pcs::build_twiddles(H > W ? H : W, tw);
-        if ((e = cudaMemcpyAsync(d.dtab, dtab.data(), dtab.size() * sizeof(float), cudaMemcpyHostToDevice, stream)) !=
-                cudaSuccess ||
-            (e = cudaMemcpyAsync(d.ddtab, ddtab.data(), ddtab.size() * sizeof(float), cudaMemcpyHostToDevice,
-                                 stream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(d.twid, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, stream)) !=
+        pcs::build_twiddles(H, tw);
+        if (dtab.size() != (size_t)(H / 2) * H || ddtab.size() != (size_t)H || tw.size() != (size_t)H)
+            return pcs::set_last_error(PCS_ECUDA, "pcs_solve_slices_noalloc: table size mismatch");
+        if (!d.tables[k_size][b0_axis] &&
+            ((e = cudaMemcpyAsync(dtab_r, dtab.data(), dtab.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                  stream)) != cudaSuccess ||
+             (e = cudaMemcpyAsync(ddtab_r, ddtab.data(), ddtab.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                  stream)) != cudaSuccess))
+            return err(PCS_ECUDA, "table upload", e);
+        if (!d.twiddles[k_size] &&
+            (e = cudaMemcpyAsync(twid_r, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, stream)) !=
                 cudaSuccess)
             return err(PCS_ECUDA, "table upload", e);
         // the host vectors die at scope exit: wait for the copies to read them
         if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return err(PCS_ECUDA, "stream sync", e);
-        d.tab_H = H;
-        d.tab_W = W;
-        d.tab_b0 = b0_axis;
+        d.tables[k_size][b0_axis] = true;
+        d.twiddles[k_size] = true;
     }
 
     const size_t n = (size_t)S * H * W;
@@ -172,9 +214,9 @@ extern "C" pcs_status pcs_solve_slices_noalloc(const float* field, const unsigne
     prm.p = d.state + n;
     prm.qx = d.state + 2 * n;
     prm.qy = d.state + 3 * n;
-    prm.dtab = d.dtab;
-    prm.ddtab = d.ddtab;
-    prm.twid = d.twid;
+    prm.dtab = dtab_r;
+    prm.ddtab = ddtab_r;
+    prm.twid = twid_r;
     prm.S = S;
     prm.n_iter = n_iter;
     prm.sigma = (float)sigma;
