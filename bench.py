@@ -39,6 +39,10 @@ WORKLOAD = "256x256x64 slices, 500 PD iterations, lambda=5e-4 (seeds/needles pha
 ALG_BYTES_PER_VOXEL_ITER = 37  # read+write chi, p, qx, qy (4 x 8 B) + read dB (4 B) + mask (1 B)
 ALG_FLOPS_PER_VOXEL_ITER = 10 * 16 + 30  # 2 real 2-D FFT round trips (10 log2(HW)) + pointwise/stencil
 L2_FLUSH_BYTES = 256 << 20
+# What ncu shows limiting the fused iteration kernel (profiles/pd_cluster_kernel_256x256x64.txt): the
+# slices in flight stay in L2, DRAM is nearly idle, and the row phases wait on L2 and distributed
+# shared-memory round trips; the HBM figure below is the useful-bytes roofline of the target.
+LIMITER_2D = "latency of L2 and DSMEM round trips (L2-resident working set; DRAM ~3% busy)"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pd_cluster_kernel_256x256x64.txt")
 
 
@@ -151,25 +155,99 @@ def cpu_oracle_sample(pb, tau, sigma, n_slices, n_iter):
     for s in range(n_slices):  # the paper's CPU method: one slice after another
         O.pd_solve(f[s], m[s], pb.lam, tau, sigma, n_iter)
     dt = time.perf_counter() - t0
-    return n_slices * H * W * n_iter / dt, dt
+    return n_slices * f.shape[-2] * f.shape[-1] * n_iter / dt, dt
+
+
+def _oracle_slice(args):
+    """One oracle slice solve (a worker of the all-cores CPU baseline); returns its seconds."""
+    import numpy as np
+
+    from oracle import pd_oracle as O
+
+    f, m, lam, tau, sigma, n_iter = args
+    t0 = time.perf_counter()
+    O.pd_solve(np.asarray(f, np.float64), m, lam, tau, sigma, n_iter)
+    return time.perf_counter() - t0
+
+
+def host_description():
+    """Host CPU model and core count (the CPU baseline's hardware)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def cpu_oracle_all_cores(fields, masks, lam, tau, sigma, n_iter, pool):
+    """The oracle over independent slices on every host core (a spawn process pool, one slice per
+    task, one numpy thread per process); returns (voxel-iter/s, wall seconds, processes)."""
+    tasks = [(fields[k], masks[k], lam, tau, sigma, n_iter) for k in range(len(fields))]
+    t0 = time.perf_counter()
+    list(pool.imap_unordered(_oracle_slice, tasks))
+    dt = time.perf_counter() - t0
+    vox = sum(int(f.size) for f in fields)
+    return vox * n_iter / dt, dt, pool._processes
+
+
+def make_oracle_pool():
+    """Process pool for the all-cores CPU baseline: spawned (never forked from a process holding a
+    CUDA context), one single-threaded numpy per process, created before the first GPU call."""
+    import multiprocessing as mp
+
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    n = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(n)
+    pool.map(_oracle_slice, [(np_zeros8(), np_ones8(), 1.0, 0.3, 0.3, 1)] * n)  # workers imported and warm
+    return pool
+
+
+def np_zeros8():
+    import numpy as np
+
+    return np.zeros((8, 8))
+
+
+def np_ones8():
+    import numpy as np
+
+    return np.ones((8, 8), np.uint8)
+
+
+PAPER_SPEEDUP = "4~15x whole-volume CPU -> GPU (Sec. III; the paper names no CPU or GPU model)"
 
 
 def run_reference(args):
+    """The oracle (this method's reference implementation) timed on every host core: each step
+    solves one slice per core of the workload, 100 iterations each, in a spawn process pool."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import phantoms
     from oracle import pd_oracle as O
 
+    pool = make_oracle_pool()
     pb = phantoms.config2(SLICES)
     L, tau, sigma = O.step_sizes(H, W)
-    n_sl, n_it = 1, 100  # bounded sample per step
+    n_sl = min(pool._processes, SLICES)
+    n_it = 100  # bounded sample per step
     for _ in range(args.warmup):
-        cpu_oracle_sample(pb, tau, sigma, n_sl, 10)
+        cpu_oracle_all_cores(pb.field[:n_sl], pb.mask[:n_sl], pb.lam, tau, sigma, 10, pool)
     times = []
     for _ in range(args.steps):
-        _, dt = cpu_oracle_sample(pb, tau, sigma, n_sl, n_it)
+        _, dt, nproc = cpu_oracle_all_cores(pb.field[:n_sl], pb.mask[:n_sl], pb.lam, tau, sigma, n_it, pool)
         times.append(dt)
+    pool.close()
     value = n_sl * H * W * n_it * len(times) / sum(times)
     line = {
         "impl": "reference",
@@ -186,8 +264,9 @@ def run_reference(args):
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "H": H, "W": W, "slices": SLICES, "n_iter": N_ITER},
-        "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{n_sl} slice x {n_it} iterations per step of the 256x256x64 workload"},
+        "cpu_baseline": {"value": value, "unit": "voxel-iter/s", "cores": nproc, "kind": "oracle",
+                         "sample": f"{n_sl} slices x {n_it} iterations per step of the 256x256x64 workload, "
+                                   "one slice per process", **host_description()},
         "e2e": {"value": value, "unit": "voxel-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -203,6 +282,7 @@ def run_native(args):
     from paper_2006_09808_gb300.sharding import max_over_ranks
 
     ws, rank, local = dist_env()
+    pool = make_oracle_pool() if (rank == 0 and not args.no_cpu_baseline) else None  # before any GPU call
     if ws > 1:
         import torch.distributed as dist
 
@@ -235,6 +315,8 @@ def run_native(args):
         flush.fill_(1.0)
         step()
     torch.cuda.synchronize()
+    pcs.pcs_check(ctx)  # a balanced-schedule wait that gave up would raise PCS_ETIMEOUT here
+    chi_warm = chi.clone()
 
     def barrier():
         if dist is not None:
@@ -254,6 +336,8 @@ def run_native(args):
         barrier()
         t_wall = time.perf_counter() - t_wall
     dev_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    pcs.pcs_check(ctx)  # every timed solve completed its schedule (else PCS_ETIMEOUT: the run fails)
+    assert torch.equal(chi, chi_warm), "a timed solve differs from the warm-up solve"
     ms_step = sum(dev_ms) / len(dev_ms)
     ms_step = max_over_ranks(ms_step, device=dev)  # slowest rank sets the job time
     work = SLICES * H * W * N_ITER  # voxel-iterations per rank per step
@@ -272,7 +356,7 @@ def run_native(args):
         pcs.pcs_solve_slices_host(ctx, hf, hm, LAM, tau, sigma, N_ITER, hc)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = sum(e2e_t) / len(e2e_t)
-    e2e_s = max_over_ranks(e2e_s, device=dev)
+    e2e_s = max_over_ranks(e2e_s, device=dev)  # (pcs_solve_slices_host checks the schedule itself)
     dev_chi = chi.cpu().numpy()
     assert np.array_equal(dev_chi, hc), "host-buffer path differs from the device path"
 
@@ -328,10 +412,12 @@ def run_native(args):
                 "threads": args.threads or "default",
             },
             "roofline": {
-                "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "bound": "latency (L2/DSMEM)", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
+                "frac_of": "the measured HBM copy peak, in useful bytes (37 B per voxel-iteration)",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "alg_bytes_per_voxel_iter": ALG_BYTES_PER_VOXEL_ITER,
+                "limiter": LIMITER_2D,
                 "fp32_alu": {"achieved_tflops": alu_achieved, "peak_tflops": fp32_peak,
                              "frac": alu_achieved / fp32_peak,
                              "alg_flops_per_voxel_iter": ALG_FLOPS_PER_VOXEL_ITER},
@@ -346,13 +432,22 @@ def run_native(args):
             "wall_s_timed_region": t_wall,
             "L": L,
         }
-        if not args.no_cpu_baseline:
-            from oracle import pd_oracle as O  # noqa: F401  (cpu_baseline leg only)
-
+        if pool is not None:
             cv, dt = cpu_oracle_sample(pb, tau, sigma, 4, N_ITER)
+            n_all = pool._processes
+            av, adt, nproc = cpu_oracle_all_cores(pb.field[:n_all], pb.mask[:n_all], pb.lam, tau, sigma, N_ITER, pool)
+            host = host_description()
             line["cpu_baseline"] = {"value": cv, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"4 slices x {N_ITER} iterations of this workload ({dt:.1f} s)"}
+                                    "sample": f"4 slices x {N_ITER} iterations of this workload ({dt:.1f} s), "
+                                              "one core (the paper's sequential CPU method)",
+                                    "all_cores": {"value": av, "unit": "voxel-iter/s", "cores": nproc,
+                                                  "sample": f"{n_all} slices x {N_ITER} iterations, one slice per "
+                                                            f"process ({adt:.1f} s wall)"},
+                                    **host}
+            line["speedup_vs_cpu"] = {"one_core": value / cv, "all_cores": value / av, "paper": PAPER_SPEEDUP}
         print(json.dumps(line), flush=True)
+    if pool is not None:
+        pool.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -629,6 +724,203 @@ def run_fieldmap(args):
     return 0
 
 
+def _gen_volume(sp):
+    """One volume of the uneven-batch recipe (a worker of the generation pool)."""
+    import phantoms
+
+    pb = phantoms.volume(sp["size"], sp["size"], sp["slices"], seed=sp["seed"], lam=sp["lam"], n_iter=sp["n_iter"])
+    return pb.field, pb.mask
+
+
+def run_uneven(args):
+    """Uneven batch: 48 volumes of 128^2..512^2 slices (16-96 slices each, lambda in {2e-4, 5e-4,
+    1e-3}), 400 iterations, solved by one pcs_batch_solve call per step (one persistent launch
+    per slice size, autotuned variants).  Compared with a per-volume loop (one pcs_solve_slices
+    per volume, one after another) and a per-slice loop (one launch per slice, timed on a
+    stratified subset and extrapolated by voxel-iterations per size)."""
+    import numpy as np
+    import torch
+
+    import paper_2006_09808_gb300 as pcs
+    import phantoms
+
+    ws, rank, local = dist_env()
+    pool = make_oracle_pool() if (rank == 0 and not args.no_cpu_baseline) else None  # before any GPU call
+    specs = phantoms.config4_volumes()
+    n_iter = specs[0]["n_iter"]
+    if pool is not None:
+        data = pool.map(_gen_volume, specs)
+    else:
+        data = [_gen_volume(sp) for sp in specs]
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pcs.load_library()
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    fields = [torch.from_numpy(f).to(dev) for f, _ in data]
+    masks = [torch.from_numpy(m).to(dev) for _, m in data]
+    chis = [torch.empty_like(f) for f in fields]
+    vols = [(fields[k], masks[k], specs[k]["lam"], chis[k]) for k in range(len(specs))]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sizes = sorted({sp["size"] for sp in specs})
+    vi_size = {n: sum(sp["slices"] * n * n * n_iter for sp in specs if sp["size"] == n) for n in sizes}
+    work = sum(vi_size.values())
+
+    batch = pcs.pcs_batch_create(autotune=True, stream=stream)
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        pcs.pcs_batch_solve(batch, vols, n_iter)
+    torch.cuda.synchronize()
+    pcs.pcs_batch_check(batch)
+    warm = [c.clone() for c in chis]
+    tun = {n: pcs.pcs_batch_tuning(batch, n, n) for n in sizes}
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            pcs.pcs_batch_solve(batch, vols, n_iter)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    pcs.pcs_batch_check(batch)
+    assert all(torch.equal(a, b) for a, b in zip(chis, warm)), "a timed batch differs from the warm-up batch"
+    ms_step = sum(s_.elapsed_time(e) for s_, e in zip(starts, ends)) / args.steps
+
+    # end to end: pinned host inputs in, chi out, around the same call
+    hf = [torch.from_numpy(f).pin_memory() for f, _ in data]
+    hm = [torch.from_numpy(m).pin_memory() for _, m in data]
+    hc = [torch.empty(f.shape, dtype=torch.float32).pin_memory() for f, _ in data]
+    e2e = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b in zip(fields, hf):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(masks, hm):
+            a.copy_(b, non_blocking=True)
+        pcs.pcs_batch_solve(batch, vols, n_iter)
+        for a, b in zip(hc, chis):
+            a.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    pcs.pcs_batch_check(batch)
+    assert all(torch.equal(a, b.cpu()) for a, b in zip(hc, warm))
+
+    # per-volume loop: one pcs_solve_slices per volume (the batch's variant of its size), in turn
+    def tuned_ctx(n, S):  # the variant the batch's autotuner chose for this size
+        t = tun[n]
+        return pcs.pcs_create(n, n, S, cluster_size=t["cluster_size"], kernel=t["kernel"], threads=t["threads"],
+                              stream=stream)
+
+    ctxs = {n: tuned_ctx(n, max(sp["slices"] for sp in specs if sp["size"] == n)) for n in sizes}
+    flush.fill_(0.5)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    outs = [torch.empty_like(f) for f in fields]
+    for k, sp in enumerate(specs):
+        L = tun[sp["size"]]["L"]
+        pcs.pcs_solve_slices(ctxs[sp["size"]], fields[k], masks[k], sp["lam"], 1 / L, 1 / L, n_iter, outs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    for c in ctxs.values():
+        pcs.pcs_check(c)
+    ms_volumes = t0.elapsed_time(t1)
+    assert all(torch.equal(a, b) for a, b in zip(outs, warm)), "per-volume solves differ from the batch"
+    # per-slice loop: one launch per slice, two slices of the first volume of each size
+    per_slice_ms = 0.0
+    sub = {}
+    for n in sizes:
+        k = next(i for i, sp in enumerate(specs) if sp["size"] == n)
+        c1 = tuned_ctx(n, 1)
+        L = tun[n]["L"]
+        o1 = torch.empty_like(fields[k][:1])
+        pcs.pcs_solve_slices(c1, fields[k][:1], masks[k][:1], specs[k]["lam"], 1 / L, 1 / L, n_iter, o1)  # warm
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for s_ in range(2):
+            pcs.pcs_solve_slices(c1, fields[k][s_:s_ + 1], masks[k][s_:s_ + 1], specs[k]["lam"], 1 / L, 1 / L,
+                                 n_iter, o1)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        pcs.pcs_destroy(c1)
+        rate = 2 * n * n * n_iter / (t0.elapsed_time(t1) * 1e-3)
+        sub[n] = rate
+        per_slice_ms += vi_size[n] / rate * 1e3
+    for c in ctxs.values():
+        pcs.pcs_destroy(c)
+    pcs.pcs_batch_destroy(batch)
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        hbm_peak = float(peaks["hbm_gbs"])
+        value = work / (ms_step * 1e-3)
+        achieved = ALG_BYTES_PER_VOXEL_ITER * work / (ms_step * 1e-3) / 1e9
+        line = {
+            "metric": "PD voxel-iterations/s (uneven batch)",
+            "value": value, "unit": "voxel-iter/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "uneven batch: 48 volumes, slices 128^2..512^2, 16-96 slices each, lambda in "
+                                   "{2e-4, 5e-4, 1e-3}, 400 PD iterations, one pcs_batch_solve per step",
+                       "voxels": work // n_iter, "n_iter": n_iter,
+                       "l2": "flushed between steps (256 MiB device write); inputs 1.3 GB > L2"},
+            "roofline": {"bound": "latency (L2/DSMEM)", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac_of": "the measured HBM copy peak, in useful bytes (37 B per voxel-iteration)",
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "alg_bytes_per_voxel_iter": ALG_BYTES_PER_VOXEL_ITER},
+            "e2e": {"value": work / (sum(e2e) / len(e2e)), "unit": "voxel-iter/s",
+                    "h2d_bytes_per_step": int(sum(f.nbytes + m.nbytes for f, m in data)),
+                    "d2h_bytes_per_step": int(sum(f.nbytes for f, _ in data))},
+            "gpu_launches": args.steps * len(sizes),
+            "batched_vs_plain": {
+                "per_volume_loop": {"value": work / (ms_volumes * 1e-3), "unit": "voxel-iter/s",
+                                    "ms": ms_volumes, "note": "48 pcs_solve_slices calls, one after another"},
+                "per_slice_loop": {"value": work / (per_slice_ms * 1e-3), "unit": "voxel-iter/s",
+                                   "ms_extrapolated": per_slice_ms,
+                                   "note": "one launch per slice, timed on 2 slices per size, extrapolated"},
+                "speedup_vs_per_volume": ms_volumes / ms_step,
+                "speedup_vs_per_slice": per_slice_ms / ms_step,
+            },
+            "tuning": {str(n): {k: tun[n][k] for k in ("cluster_size", "kernel", "threads", "L")} for n in sizes},
+            "clocks": clk.summary(),
+        }
+        if pool is not None:
+            from oracle import pd_oracle as O  # noqa: F401  (cpu_baseline leg only)
+
+            one_t, all_t, nproc = 0.0, 0.0, pool._processes
+            n_cpu = 40
+            for n in sizes:
+                k = next(i for i, sp in enumerate(specs) if sp["size"] == n)
+                f, m = data[k]
+                L = tun[n]["L"]
+                t_a = time.perf_counter()
+                _oracle_slice((f[0], m[0], specs[k]["lam"], 1 / L, 1 / L, n_cpu))
+                one_t += vi_size[n] / (n * n * n_cpu / (time.perf_counter() - t_a))
+                reps = [f[s_ % f.shape[0]] for s_ in range(nproc)]
+                repm = [m[s_ % m.shape[0]] for s_ in range(nproc)]
+                av, _, _ = cpu_oracle_all_cores(reps, repm, specs[k]["lam"], 1 / L, 1 / L, n_cpu, pool)
+                all_t += vi_size[n] / av
+            line["cpu_baseline"] = {"value": work / one_t, "unit": "voxel-iter/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"one slice per size x {n_cpu} iterations, extrapolated by "
+                                              "voxel-iterations per size",
+                                    "all_cores": {"value": work / all_t, "unit": "voxel-iter/s", "cores": nproc,
+                                                  "sample": f"{nproc} slices per size x {n_cpu} iterations, one "
+                                                            "slice per process, extrapolated"},
+                                    **host_description()}
+            line["speedup_vs_cpu"] = {"one_core": value / (work / one_t), "all_cores": value / (work / all_t),
+                                      "paper": PAPER_SPEEDUP}
+        print(json.dumps(line), flush=True)
+    if pool is not None:
+        pool.close()
+    return 0
+
+
 def run_serve(args):
     """Serving leg: Poisson arrivals of uneven-batch-style volumes, streamed slice by slice."""
     import heapq
@@ -740,10 +1032,11 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
     ap.add_argument("--plain-loop", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the plain per-slice GPU loop (one timed volume)")
-    ap.add_argument("--workload", choices=["volume", "serve", "volume3d", "fieldmap", "native"], default="volume",
+    ap.add_argument("--workload", choices=["volume", "serve", "volume3d", "fieldmap", "native", "uneven"],
+                    default="volume",
                     help="volume: the 256x256x64 solve (default); serve: the serving loop; "
                          "volume3d: the 3-D variant on the same volume; fieldmap: the preprocessing step; "
-                         "native: the any-size path on 25 slices of 256x258")
+                         "native: the any-size path on 25 slices of 256x258; uneven: the 48-volume uneven batch")
     ap.add_argument("--requests", type=int, default=80, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
     ap.add_argument("--baseline-requests", type=int, default=20, help="serving: requests in the plain baseline")
@@ -758,6 +1051,8 @@ def main():
         return run_fieldmap(args)
     if args.workload == "native":
         return run_native_shape(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
     return run_native(args)
 
 
