@@ -957,6 +957,8 @@ def run_serve(args):
             if s1 > s0:
                 heapq.heappush(events, (r["t"] + 0.1 * (c + 1) / n_chunks, 2 * i + 1, "push", i, s0, s1 - s0))
     ids, done = {}, {}
+    rid_to_i = {}
+    check_every = 50  # these requests' chi is kept and compared with the per-request solves
     t0 = time.perf_counter()
     while events or len(done) < len(reqs):
         now = time.perf_counter() - t0
@@ -967,18 +969,23 @@ def run_serve(args):
             if kind == "open":
                 outs[i] = torch.empty((S, H, H), dtype=torch.float32).pin_memory().numpy()
                 ids[i] = pcs.pcs_serve_open(sv, H, H, S, r["lam"], outs[i])
+                rid_to_i[ids[i]] = i
             else:
                 f, m = pool[H]
                 pcs.pcs_serve_push(sv, ids[i], s0, f[s0:s0 + n], m[s0:s0 + n])
-        for rid, lat in pcs.pcs_serve_poll(sv):
+        for rid, lat, st_ in pcs.pcs_serve_poll(sv):
+            if st_ != pcs.PCS_OK:
+                raise RuntimeError(f"request {rid} failed with status {st_}")
             done[rid] = lat
+            if rid_to_i[rid] % check_every:
+                outs.pop(rid_to_i[rid])  # release the pinned output (only sampled requests are kept)
         time.sleep(0.0005)
     st = pcs.pcs_serve_stats(sv)
     pcs.pcs_serve_stop(sv)
     vox_iters = sum(r["slices"] * r["size"] ** 2 * n_iter for r in reqs)
     window = reqs[-1]["t"] - reqs[0]["t"]
     # baseline: the same requests solved one after another with plain per-request calls
-    base_reqs = reqs[: args.baseline_requests]
+    base_reqs = reqs[: args.baseline_requests] if args.baseline_requests > 0 else reqs
     ctxs = {}
     t_base, vi_base = 0.0, 0.0
     for r in base_reqs:
@@ -994,6 +1001,8 @@ def run_serve(args):
         pcs.pcs_solve_slices_host(ctxs[H], f[:S], m[:S], r["lam"], 1 / tun[H]["L"], 1 / tun[H]["L"], n_iter, out)
         t_base += time.perf_counter() - ta
         vi_base += S * H * H * n_iter
+        if r["idx"] in outs:  # served == per-request solve, bit for bit (same kernel variant and step)
+            assert np.array_equal(outs[r["idx"]], out), f"served request {r['idx']} differs from its plain solve"
     for c in ctxs.values():
         pcs.pcs_destroy(c)
     line = {
@@ -1037,9 +1046,10 @@ def main():
                     help="volume: the 256x256x64 solve (default); serve: the serving loop; "
                          "volume3d: the 3-D variant on the same volume; fieldmap: the preprocessing step; "
                          "native: the any-size path on 25 slices of 256x258; uneven: the 48-volume uneven batch")
-    ap.add_argument("--requests", type=int, default=80, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=400, help="serving: number of requests (the 400-request window)")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
-    ap.add_argument("--baseline-requests", type=int, default=20, help="serving: requests in the plain baseline")
+    ap.add_argument("--baseline-requests", type=int, default=0,
+                    help="serving: requests in the per-request baseline (0: all of them)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -394,7 +394,8 @@ PCS_API void pcs_batch_destroy(pcs_batch *b);
 typedef struct pcs_server pcs_server; /* opaque */
 
 typedef struct pcs_server_config {
-    size_t hbm_budget_bytes; /* device memory the admitted requests may hold (25 B per voxel) */
+    size_t hbm_budget_bytes; /* device memory the admitted requests may hold (see pcs_serve_request_bytes);
+                                allocated once, as one arena, by pcs_serve_start */
     int slots;               /* requests in flight at once (one CUDA stream each) */
     int n_iter;              /* primal-dual iterations per slice */
     int autotune;            /* pick each slice size's kernel variant by timing (see pcs_batch_create) */
@@ -408,8 +409,9 @@ typedef struct pcs_serve_summary {
     double voxel_iters;      /* sum over finished requests of S*H*W*n_iter */
     double span_s;           /* first open -> last completion */
     double p50_s, p99_s, max_s; /* per-volume latency (open -> last slice back on the host) */
-    double peak_bytes;       /* peak budget in use */
+    double peak_bytes;       /* peak bytes of the arena held by admitted requests */
     int peak_inflight, pad;
+    long long failed;        /* requests finished with an error status */
 } pcs_serve_summary;
 
 /*
@@ -419,6 +421,11 @@ typedef struct pcs_serve_summary {
  * a request's primal/dual state stays on the device until it completes),
  * and copies chi back into the request's host buffer.  Slices are solved
  * independently, so a volume's chi does not depend on what else is in flight.
+ * The budget is allocated here as one device arena (PCS_ENOMEM if it cannot
+ * be); admitted requests occupy ranges of it, so the scheduler thread never
+ * allocates or frees device memory while serving.  A request whose copy or
+ * launch fails finishes alone with an error status (pcs_serve_poll); a
+ * sticky CUDA error stops the server and every later poll returns it.
  */
 PCS_API pcs_status pcs_serve_start(pcs_server **out, const pcs_server_config *cfg);
 
@@ -430,8 +437,10 @@ PCS_API pcs_status pcs_serve_prepare_size(pcs_server *sv, int H, int W, pcs_tuni
  * chi_host: host [S][H][W] float32 that receives chi (keep it alive until the
  * request completes).  Returns its id.  PCS_ENOMEM if the volume alone exceeds
  * the budget, PCS_EUNSUPPORTED for a size neither compiled nor accepted by
- * pcs_supported_generic (those run the any-size kernels, each slot with its own
- * half-spectrum scratch, counted in the budget).
+ * pcs_supported_generic (those run the any-size kernels, each request with its
+ * own half-spectrum scratch, counted in the budget).  The first request of a
+ * slice size not prepared with pcs_serve_prepare_size sets that size up on the
+ * calling thread (autotuning and step size: up to about a second).
  */
 PCS_API pcs_status pcs_serve_open(pcs_server *sv, int H, int W, int S, double lambda, float *chi_host,
                                   long long *id);
@@ -444,8 +453,24 @@ PCS_API pcs_status pcs_serve_open(pcs_server *sv, int H, int W, int S, double la
 PCS_API pcs_status pcs_serve_push(pcs_server *sv, long long id, int s0, int n, const float *field_host,
                                   const unsigned char *mask_host);
 
-/* Up to max finished requests since the last poll: ids and latencies (s). Non-blocking. */
-PCS_API pcs_status pcs_serve_poll(pcs_server *sv, long long *ids, double *latency_s, int max, int *n_out);
+/*
+ * Up to max finished requests since the last poll: ids, latencies (s) and,
+ * if status is not NULL, each request's status (PCS_OK, or PCS_ECUDA for a
+ * request whose copy or launch failed; its chi is incomplete).  Non-blocking.
+ * Returns PCS_ECUDA once the server met a sticky CUDA error.
+ */
+PCS_API pcs_status pcs_serve_poll(pcs_server *sv, long long *ids, double *latency_s, pcs_status *status, int max,
+                                  int *n_out);
+
+/* Device bytes one request of S slices of H x W holds while admitted (its share of the budget). */
+PCS_API pcs_status pcs_serve_request_bytes(int H, int W, int S, size_t *bytes);
+
+/*
+ * Failure injection on the host (tests): the next launch of request id reports
+ * an error code as if the launch call had failed, so that the request fails
+ * alone.  No GPU fault is involved.
+ */
+PCS_API pcs_status pcs_serve_fail_next_launch(pcs_server *sv, long long id);
 
 /* Running statistics (latency quantiles over finished requests). */
 PCS_API pcs_status pcs_serve_stats(pcs_server *sv, pcs_serve_summary *out);

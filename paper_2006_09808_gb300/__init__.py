@@ -121,6 +121,7 @@ class pcs_serve_summary(ctypes.Structure):
         ("peak_bytes", ctypes.c_double),
         ("peak_inflight", ctypes.c_int),
         ("pad", ctypes.c_int),
+        ("failed", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -176,7 +177,10 @@ def load_library(path: str = LIB_PATH):
         "pcs_serve_prepare_size": (i, [vp, i, i, ctypes.POINTER(pcs_tuning)]),
         "pcs_serve_open": (i, [vp, i, i, i, d, vp, ctypes.POINTER(ctypes.c_longlong)]),
         "pcs_serve_push": (i, [vp, ctypes.c_longlong, i, i, vp, vp]),
-        "pcs_serve_poll": (i, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d), i, ctypes.POINTER(i)]),
+        "pcs_serve_poll": (i, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d), ctypes.POINTER(i), i,
+                               ctypes.POINTER(i)]),
+        "pcs_serve_request_bytes": (i, [i, i, i, ctypes.POINTER(ctypes.c_size_t)]),
+        "pcs_serve_fail_next_launch": (i, [vp, ctypes.c_longlong]),
         "pcs_serve_stats": (i, [vp, ctypes.POINTER(pcs_serve_summary)]),
         "pcs_serve_stop": (None, [vp]),
         "pcs_last_error": (ctypes.c_char_p, []),
@@ -546,11 +550,25 @@ def pcs_serve_push(server, rid: int, s0: int, field_host, mask_host):
 
 
 def pcs_serve_poll(server, max_items: int = 256):
+    """Finished requests since the last poll: [(id, latency_s, status)], status PCS_OK or an error code."""
     ids = (ctypes.c_longlong * max_items)()
     lat = (ctypes.c_double * max_items)()
+    st = (ctypes.c_int * max_items)()
     n = ctypes.c_int()
-    _check(load_library().pcs_serve_poll(server, ids, lat, max_items, ctypes.byref(n)), "pcs_serve_poll")
-    return [(ids[k], lat[k]) for k in range(n.value)]
+    _check(load_library().pcs_serve_poll(server, ids, lat, st, max_items, ctypes.byref(n)), "pcs_serve_poll")
+    return [(ids[k], lat[k], st[k]) for k in range(n.value)]
+
+
+def pcs_serve_request_bytes(H: int, W: int, S: int) -> int:
+    """Device bytes one request holds while admitted (its share of the server's budget)."""
+    out = ctypes.c_size_t()
+    _check(load_library().pcs_serve_request_bytes(H, W, S, ctypes.byref(out)), "pcs_serve_request_bytes")
+    return out.value
+
+
+def pcs_serve_fail_next_launch(server, rid: int):
+    """Host-side failure injection (tests): the next launch of request rid reports an error."""
+    _check(load_library().pcs_serve_fail_next_launch(server, rid), "pcs_serve_fail_next_launch")
 
 
 def pcs_serve_stats(server):

@@ -2,18 +2,26 @@
 //
 // A volume request (S slices of H x W, its lambda) is opened with
 // pcs_serve_open and its slices arrive over time (pcs_serve_push: an
-// interventional scan streaming slices).  A scheduler thread owned by the
+// interventional scan streaming slices).  The server allocates one device
+// arena of the HBM budget when it starts; a scheduler thread owned by the
 // server
 //   * admits open requests in arrival order when a slot (a CUDA stream) is
-//     free and the request's device footprint fits the HBM budget
-//     (field + mask + chi + the four state arrays: 25 B per voxel);
+//     free and the request's device footprint (field + mask + chi + the four
+//     state arrays, 25 B per voxel, plus the half spectrum for sizes run by
+//     the any-size kernels) fits in a free range of the arena -- the budget is
+//     exactly the memory the requests hold, and the scheduler thread never
+//     allocates or frees device memory;
 //   * as soon as slices of an admitted request have arrived, copies them to
 //     the device and launches the fused iteration kernel on them (slices are
 //     independent, so solving them in chunks gives the same chi as solving the
 //     volume at once); chunks of different requests run concurrently on
 //     their slots' streams;
 //   * copies chi back, and when every slice of a request is done, records its
-//     latency (completion - open) and frees its budget.
+//     latency (completion - open) and returns its range to the arena.
+// A request whose copy or launch fails is finished alone with that status
+// (its remaining slices are not launched); the other requests go on.  A
+// sticky CUDA error (a device fault) ends the server: pcs_serve_poll
+// reports it.
 // Step sizes are tau = sigma = 1/L(H, W) (Sec. II.A pseudocode step 1), L the
 // full-mask operator norm, computed once per slice size; the kernel variant
 // of each size is the one the batch autotuner picks.  The primal/dual state of
@@ -24,8 +32,10 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdint>
 #include <cstring>
 #include <deque>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -95,8 +105,63 @@ struct SizeInfo {
 
 struct Chunk {
     int s0, n;
-    cudaEvent_t done;
+    cudaEvent_t done;  // recorded after the chunk's copies and launch
+    bool ok;           // false: a copy or launch of the chunk failed (its slices are dropped)
 };
+
+// First-fit allocator of byte ranges inside the server's device arena (host bookkeeping only).
+class Arena {
+  public:
+    static constexpr size_t kAlign = 256;
+    void reset(size_t cap) {
+        free_.clear();
+        if (cap) free_[0] = cap;
+        used_ = 0;
+    }
+    // offset of a free range of `bytes` (a multiple of kAlign), or SIZE_MAX
+    size_t alloc(size_t bytes) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const size_t off = it->first, len = it->second;
+            free_.erase(it);
+            if (len > bytes) free_[off + bytes] = len - bytes;
+            used_ += bytes;
+            return off;
+        }
+        return SIZE_MAX;
+    }
+    void release(size_t off, size_t bytes) {
+        used_ -= bytes;
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + bytes == nx->first) {  // merge with the next range
+            bytes += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {  // merge with the previous range
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                pv->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+    size_t used() const { return used_; }
+
+  private:
+    std::map<size_t, size_t> free_;  // offset -> length
+    size_t used_ = 0;
+};
+
+size_t align_up(size_t n) { return (n + Arena::kAlign - 1) / Arena::kAlign * Arena::kAlign; }
+
+// Device bytes a request holds: field, mask, chi, chibar/p/qx/qy and (any-size kernels) the half
+// spectrum, each range 256-byte aligned.
+size_t request_bytes(int H, int W, int S) {
+    const size_t vox = (size_t)S * H * W;
+    return align_up(vox * 4) + align_up(vox) + align_up(vox * 4) + align_up(4 * vox * 4) +
+           align_up(spec_bytes(H, W, vox));
+}
 
 struct Request {
     long long id = 0;
@@ -111,22 +176,24 @@ struct Request {
         const unsigned char* mask;
     };
     std::deque<Arrival> arrived;
-    int pushed = 0, launched = 0, completed = 0;
+    int pushed = 0, launched = 0, completed = 0, dropped = 0;
     int slot = -1;  // -1 while waiting for admission
     size_t bytes = 0;
+    size_t arena_off = SIZE_MAX;  // its range of the arena once admitted
+    // device buffers inside that range
+    float* field = nullptr;
+    unsigned char* mask = nullptr;
+    float* chi = nullptr;
+    float* state = nullptr;  // chibar, p, qx, qy
+    float2* spec = nullptr;  // half spectrum, for sizes run by the any-size kernels
+    pcs_status st = PCS_OK;  // a failed copy or launch finishes the request with this status
+    bool fail_next = false;  // host-side fault injection (tests): the next launch reports failure
     std::vector<Chunk> chunks;  // launched, not yet completed
 };
 
 struct Slot {
     cudaStream_t stream = nullptr;
     long long req = -1;  // request occupying the slot
-    // device arena of the occupying request
-    float* field = nullptr;
-    unsigned char* mask = nullptr;
-    float* chi = nullptr;
-    float* state = nullptr;  // chibar, p, qx, qy
-    float2* spec = nullptr;  // half spectrum, for sizes run by the any-size kernels
-    size_t cap_voxels = 0, cap_spec = 0;
 };
 
 }  // namespace
@@ -143,9 +210,16 @@ struct pcs_server {
     std::deque<long long> admit_queue;  // open requests in arrival order, not yet admitted
     std::vector<Slot> slots;
     std::map<std::pair<int, int>, SizeInfo> sizes;
-    size_t bytes_in_use = 0;
-    // completions not yet polled: (id, latency s)
-    std::deque<std::pair<long long, double>> done;
+    char* arena_base = nullptr;  // one device allocation of hbm_budget_bytes, made at start
+    Arena arena;
+    std::vector<cudaEvent_t> events;  // pool of chunk-completion events (created at start, reused)
+    // completions not yet polled: (id, latency s, status)
+    struct Done {
+        long long id;
+        double latency;
+        pcs_status st;
+    };
+    std::deque<Done> done;
     // statistics
     Clock::time_point t_first_open;
     bool any_open = false;
@@ -155,13 +229,12 @@ struct pcs_server {
     std::vector<double> latencies;
     int peak_inflight = 0;
     size_t peak_bytes = 0;
-    pcs_status worker_error = PCS_OK;
+    long long n_failed = 0;
+    pcs_status worker_error = PCS_OK;  // server-level (sticky) CUDA error
     std::string worker_error_text;
 };
 
 namespace {
-
-constexpr size_t kBytesPerVoxel = 4 + 1 + 4 + 16;  // field, mask, chi, 4 state arrays
 
 pcs_status size_setup(pcs_server* sv, int H, int W, SizeInfo** out) {
     auto key = std::make_pair(H, W);
@@ -230,20 +303,7 @@ pcs_status size_setup(pcs_server* sv, int H, int W, SizeInfo** out) {
     return PCS_OK;
 }
 
-void slot_release(Slot& sl) {
-    void* p[] = {sl.field, sl.mask, sl.chi, sl.state, sl.spec};
-    for (void* q : p)
-        if (q) cudaFree(q);
-    sl.field = nullptr;
-    sl.mask = nullptr;
-    sl.chi = nullptr;
-    sl.state = nullptr;
-    sl.spec = nullptr;
-    sl.cap_voxels = 0;
-    sl.cap_spec = 0;
-}
-
-// Admit waiting requests (arrival order) while a slot and budget are free.
+// Admit waiting requests (arrival order) while a slot and a large enough arena range are free.
 void admit(pcs_server* sv) {
     while (!sv->admit_queue.empty()) {
         const long long id = sv->admit_queue.front();
@@ -260,25 +320,23 @@ void admit(pcs_server* sv) {
                 break;
             }
         if (free_slot < 0) return;
-        if (sv->bytes_in_use + r.bytes > sv->cfg.hbm_budget_bytes) return;  // wait for memory
-        Slot& sl = sv->slots[free_slot];
+        const size_t off = sv->arena.alloc(r.bytes);
+        if (off == SIZE_MAX) return;  // wait for memory (arrival order: no overtaking)
+        r.arena_off = off;
         const size_t vox = (size_t)r.S * r.H * r.W;
-        const size_t sb = spec_bytes(r.H, r.W, vox);
-        if (sl.cap_voxels < vox || sl.cap_spec < sb) {
-            slot_release(sl);
-            if (cudaMalloc(&sl.field, vox * 4) != cudaSuccess || cudaMalloc(&sl.mask, vox) != cudaSuccess ||
-                cudaMalloc(&sl.chi, vox * 4) != cudaSuccess || cudaMalloc(&sl.state, 4 * vox * 4) != cudaSuccess ||
-                (sb > 0 && cudaMalloc(&sl.spec, sb) != cudaSuccess)) {
-                slot_release(sl);
-                return;  // device memory exhausted beyond the budget: retry later
-            }
-            sl.cap_voxels = vox;
-            sl.cap_spec = sb;
-        }
-        sl.req = id;
+        char* p = sv->arena_base + off;
+        r.field = reinterpret_cast<float*>(p);
+        p += align_up(vox * 4);
+        r.mask = reinterpret_cast<unsigned char*>(p);
+        p += align_up(vox);
+        r.chi = reinterpret_cast<float*>(p);
+        p += align_up(vox * 4);
+        r.state = reinterpret_cast<float*>(p);
+        p += align_up(4 * vox * 4);
+        r.spec = spec_bytes(r.H, r.W, vox) ? reinterpret_cast<float2*>(p) : nullptr;
+        sv->slots[free_slot].req = id;
         r.slot = free_slot;
-        sv->bytes_in_use += r.bytes;
-        sv->peak_bytes = std::max(sv->peak_bytes, sv->bytes_in_use);
+        sv->peak_bytes = std::max(sv->peak_bytes, sv->arena.used());
         sv->admit_queue.pop_front();
         int inflight = 0;
         for (auto& s : sv->slots) inflight += s.req >= 0;
@@ -286,103 +344,142 @@ void admit(pcs_server* sv) {
     }
 }
 
-// Launch every arrived slice range of admitted requests.
+// Launch every arrived slice range of admitted requests.  A request whose copy or launch fails
+// gets that status; its later slices are dropped.
 bool launch_arrived(pcs_server* sv) {
     bool any = false;
     for (auto& kv : sv->reqs) {
         Request& r = kv.second;
         if (r.slot < 0 || r.arrived.empty()) continue;
         Slot& sl = sv->slots[r.slot];
-        SizeInfo* si = nullptr;
-        if (size_setup(sv, r.H, r.W, &si) != PCS_OK) {
-            sv->worker_error = PCS_ECUDA;
-            sv->worker_error_text = "size set-up failed";
-            continue;
-        }
+        auto sit = sv->sizes.find(std::make_pair(r.H, r.W));
+        SizeInfo* si = sit == sv->sizes.end() ? nullptr : &sit->second;  // set up when the request opened
         const size_t slice = (size_t)r.H * r.W;
         const size_t vox = (size_t)r.S * slice;
         while (!r.arrived.empty()) {
             Request::Arrival a = r.arrived.front();
             r.arrived.pop_front();
+            any = true;
+            if (r.st != PCS_OK || !si) {  // a failed request launches nothing more
+                if (r.st == PCS_OK) r.st = PCS_EINVAL;
+                r.dropped += a.n;
+                continue;
+            }
             cudaError_t e1 =
-                cudaMemcpyAsync(sl.field + a.s0 * slice, a.field, a.n * slice * 4, cudaMemcpyHostToDevice, sl.stream);
-            cudaError_t e2 = cudaMemcpyAsync(sl.mask + a.s0 * slice, a.mask, a.n * slice, cudaMemcpyHostToDevice, sl.stream);
+                cudaMemcpyAsync(r.field + a.s0 * slice, a.field, a.n * slice * 4, cudaMemcpyHostToDevice, sl.stream);
+            cudaError_t e2 = cudaMemcpyAsync(r.mask + a.s0 * slice, a.mask, a.n * slice, cudaMemcpyHostToDevice, sl.stream);
             cudaError_t e3 = cudaSuccess;
             if (si->gen) {
-                // any-size kernels on this slot's stream and spectrum
+                // any-size kernels on this slot's stream and the request's spectrum
                 const double step = 1.0 / si->L;
                 const size_t sp_slice = (size_t)r.H * (r.W / 2 + 1);
-                e3 = pcs::gen_enqueue(si->gen, sl.field + a.s0 * slice, sl.mask + a.s0 * slice, nullptr,
-                                      sl.chi + a.s0 * slice, sl.state + a.s0 * slice, sl.state + vox + a.s0 * slice,
-                                      sl.state + 2 * vox + a.s0 * slice, sl.state + 3 * vox + a.s0 * slice, a.n,
+                e3 = pcs::gen_enqueue(si->gen, r.field + a.s0 * slice, r.mask + a.s0 * slice, nullptr,
+                                      r.chi + a.s0 * slice, r.state + a.s0 * slice, r.state + vox + a.s0 * slice,
+                                      r.state + 2 * vox + a.s0 * slice, r.state + 3 * vox + a.s0 * slice, a.n,
                                       r.lambda, step, step, sv->cfg.n_iter, sl.stream, 0, nullptr, nullptr,
-                                      sl.spec + a.s0 * sp_slice);
+                                      r.spec + a.s0 * sp_slice);
+            } else {
+                pcs::PDParams prm;
+                std::memset(&prm, 0, sizeof(prm));
+                prm.field = r.field + a.s0 * slice;
+                prm.mask = r.mask + a.s0 * slice;
+                prm.chi = r.chi + a.s0 * slice;
+                prm.chibar = r.state + a.s0 * slice;
+                prm.p = r.state + vox + a.s0 * slice;
+                prm.qx = r.state + 2 * vox + a.s0 * slice;
+                prm.qy = r.state + 3 * vox + a.s0 * slice;
+                prm.dtab = si->dtab;
+                prm.ddtab = si->ddtab;
+                prm.twid = si->twid;
+                prm.S = a.n;
+                prm.n_iter = sv->cfg.n_iter;
+                prm.sigma = (float)(1.0 / si->L);
+                prm.tau = (float)(1.0 / si->L);
+                prm.inv_den = (float)(1.0 / (1.0 + (1.0 / si->L) / r.lambda));
+                prm.inv_den_slice = nullptr;
+                const int ncl = std::min(si->max_clusters, a.n);
+                e3 = si->entry->launch(prm, ncl < 1 ? 1 : ncl, sl.stream);
             }
-            pcs::PDParams prm;
-            std::memset(&prm, 0, sizeof(prm));
-            prm.field = sl.field + a.s0 * slice;
-            prm.mask = sl.mask + a.s0 * slice;
-            prm.chi = sl.chi + a.s0 * slice;
-            prm.chibar = sl.state + a.s0 * slice;
-            prm.p = sl.state + vox + a.s0 * slice;
-            prm.qx = sl.state + 2 * vox + a.s0 * slice;
-            prm.qy = sl.state + 3 * vox + a.s0 * slice;
-            prm.dtab = si->dtab;
-            prm.ddtab = si->ddtab;
-            prm.twid = si->twid;
-            prm.S = a.n;
-            prm.n_iter = sv->cfg.n_iter;
-            prm.sigma = (float)(1.0 / si->L);
-            prm.tau = (float)(1.0 / si->L);
-            prm.inv_den = (float)(1.0 / (1.0 + (1.0 / si->L) / r.lambda));
-            prm.inv_den_slice = nullptr;
-            int ncl = std::min(si->max_clusters, a.n);
-            if (!si->gen) e3 = si->entry->launch(prm, ncl < 1 ? 1 : ncl, sl.stream);
-            cudaError_t e4 = cudaMemcpyAsync(r.chi_host + a.s0 * slice, sl.chi + a.s0 * slice, a.n * slice * 4,
+            if (r.fail_next) {  // injected on the host: this launch reports an error code
+                r.fail_next = false;
+                e3 = cudaErrorLaunchOutOfResources;
+            }
+            cudaError_t e4 = cudaMemcpyAsync(r.chi_host + a.s0 * slice, r.chi + a.s0 * slice, a.n * slice * 4,
                                              cudaMemcpyDeviceToHost, sl.stream);
-            if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
-                sv->worker_error = PCS_ECUDA;
-                sv->worker_error_text = "copy or launch failed in the serving loop";
+            const bool ok = e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess;
+            if (!ok) {
+                // this request fails alone; a sticky error (the context is lost) stops the server
+                r.st = PCS_ECUDA;
+                (void)cudaGetLastError();  // clears a non-sticky error
+                if (cudaGetLastError() != cudaSuccess) {
+                    sv->worker_error = PCS_ECUDA;
+                    sv->worker_error_text = "sticky CUDA error in the serving loop";
+                }
             }
-            Chunk c{a.s0, a.n, nullptr};
-            cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming);
-            cudaEventRecord(c.done, sl.stream);
+            // whatever was enqueued must finish before the request's arena range is reused
+            Chunk c{a.s0, a.n, nullptr, ok};
+            if (sv->events.empty()) {  // pool exhausted (many chunks in flight): one more event
+                cudaEvent_t ev = nullptr;
+                if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) sv->events.push_back(ev);
+            }
+            if (!sv->events.empty()) {
+                c.done = sv->events.back();
+                sv->events.pop_back();
+            }
+            if (!c.done || cudaEventRecord(c.done, sl.stream) != cudaSuccess) {
+                if (c.done) sv->events.push_back(c.done);
+                c.done = nullptr;
+                cudaStreamSynchronize(sl.stream);
+                c.ok = false;
+                r.st = PCS_ECUDA;
+            }
             r.chunks.push_back(c);
             r.launched += a.n;
-            any = true;
         }
     }
     return any;
 }
 
-// Retire finished chunks and requests.
+// Retire finished chunks and requests (a failed request once none of its chunks is in flight
+// and every slice was pushed or it can no longer complete).
 bool retire(pcs_server* sv) {
     bool any = false;
     std::vector<long long> finished;
     for (auto& kv : sv->reqs) {
         Request& r = kv.second;
         for (size_t k = 0; k < r.chunks.size();) {
-            if (cudaEventQuery(r.chunks[k].done) == cudaSuccess) {
-                r.completed += r.chunks[k].n;
-                cudaEventDestroy(r.chunks[k].done);
+            const cudaError_t q = r.chunks[k].done ? cudaEventQuery(r.chunks[k].done) : cudaSuccess;
+            if (q != cudaErrorNotReady) {
+                if (q == cudaSuccess && r.chunks[k].ok) {
+                    r.completed += r.chunks[k].n;
+                } else {
+                    r.st = PCS_ECUDA;
+                    r.dropped += r.chunks[k].n;
+                }
+                if (r.chunks[k].done) sv->events.push_back(r.chunks[k].done);  // back to the pool
                 r.chunks.erase(r.chunks.begin() + k);
                 any = true;
             } else {
                 ++k;
             }
         }
-        if (r.slot >= 0 && r.completed == r.S) finished.push_back(r.id);
+        if (r.slot < 0 || !r.chunks.empty()) continue;
+        if (r.completed == r.S || (r.st != PCS_OK && r.arrived.empty())) finished.push_back(r.id);
     }
     for (long long id : finished) {
         Request& r = sv->reqs[id];
         const double lat = seconds_since(r.t_open);
         sv->slots[r.slot].req = -1;
-        sv->bytes_in_use -= r.bytes;
-        sv->done.emplace_back(id, lat);
-        sv->latencies.push_back(lat);
-        sv->n_done++;
-        sv->voxel_iters_done += (double)r.S * r.H * r.W * sv->cfg.n_iter;
-        sv->t_last_done = seconds_since(sv->t_first_open);
+        sv->arena.release(r.arena_off, r.bytes);
+        sv->done.push_back({id, lat, r.st});
+        if (r.st == PCS_OK) {
+            sv->latencies.push_back(lat);
+            sv->n_done++;
+            sv->voxel_iters_done += (double)r.S * r.H * r.W * sv->cfg.n_iter;
+            sv->t_last_done = seconds_since(sv->t_first_open);
+        } else {
+            sv->n_failed++;
+        }
         sv->reqs.erase(id);
     }
     return any;
@@ -418,6 +515,22 @@ pcs_status pcs_serve_start(pcs_server** out, const pcs_server_config* cfg) {
     pcs_server* sv = new pcs_server();
     sv->cfg = *cfg;
     cudaGetDevice(&sv->device);
+    // the whole budget, once: requests are placed in it and the scheduler never allocates
+    const size_t cap = cfg->hbm_budget_bytes / Arena::kAlign * Arena::kAlign;
+    if (cap == 0 || cudaMalloc(&sv->arena_base, cap) != cudaSuccess) {
+        sv->arena_base = nullptr;
+        pcs_serve_stop(sv);
+        return pcs::set_last_error(PCS_ENOMEM, "pcs_serve_start: cannot allocate the budget's device arena");
+    }
+    sv->arena.reset(cap);
+    for (int k = 0; k < 16 * cfg->slots; ++k) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            pcs_serve_stop(sv);
+            return pcs::set_last_error(PCS_ECUDA, "pcs_serve_start: event create");
+        }
+        sv->events.push_back(ev);
+    }
     sv->slots.resize(cfg->slots);
     for (auto& s : sv->slots)
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -443,9 +556,14 @@ pcs_status pcs_serve_open(pcs_server* sv, int H, int W, int S, double lambda, fl
     if (!sv || !chi_host || !id) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_open: NULL argument");
     if (S < 1 || !(lambda > 0.0)) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_open: S >= 1 and lambda > 0");
     if (!served_size(H, W)) return pcs::set_last_error(PCS_EUNSUPPORTED, "pcs_serve_open: unsupported slice size");
-    const size_t bytes = (size_t)S * H * W * kBytesPerVoxel + spec_bytes(H, W, (size_t)S * H * W);
-    if (bytes > sv->cfg.hbm_budget_bytes) return pcs::set_last_error(PCS_ENOMEM, "pcs_serve_open: volume exceeds the budget");
+    const size_t bytes = request_bytes(H, W, S);
+    if (bytes > sv->cfg.hbm_budget_bytes / Arena::kAlign * Arena::kAlign)
+        return pcs::set_last_error(PCS_ENOMEM, "pcs_serve_open: volume exceeds the budget");
     std::lock_guard<std::mutex> lk(sv->mu);
+    // a new slice size is set up here, on the caller's thread (autotuning, tables, step size)
+    SizeInfo* si = nullptr;
+    pcs_status st = size_setup(sv, H, W, &si);
+    if (st != PCS_OK) return st;
     Request r;
     r.id = sv->next_id++;
     r.H = H;
@@ -480,18 +598,37 @@ pcs_status pcs_serve_push(pcs_server* sv, long long id, int s0, int n, const flo
     return PCS_OK;
 }
 
-pcs_status pcs_serve_poll(pcs_server* sv, long long* ids, double* latency_s, int max, int* n_out) {
+pcs_status pcs_serve_poll(pcs_server* sv, long long* ids, double* latency_s, pcs_status* status, int max,
+                          int* n_out) {
     if (!sv || !n_out || (max > 0 && (!ids || !latency_s))) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_poll: NULL");
     std::lock_guard<std::mutex> lk(sv->mu);
     int n = 0;
     while (n < max && !sv->done.empty()) {
-        ids[n] = sv->done.front().first;
-        latency_s[n] = sv->done.front().second;
+        ids[n] = sv->done.front().id;
+        latency_s[n] = sv->done.front().latency;
+        if (status) status[n] = sv->done.front().st;
         sv->done.pop_front();
         ++n;
     }
     *n_out = n;
-    return sv->worker_error;
+    if (sv->worker_error != PCS_OK) return pcs::set_last_error(sv->worker_error, sv->worker_error_text.c_str());
+    return PCS_OK;
+}
+
+pcs_status pcs_serve_request_bytes(int H, int W, int S, size_t* bytes) {
+    if (!bytes || S < 1) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_request_bytes: bad argument");
+    if (!served_size(H, W)) return pcs::set_last_error(PCS_EUNSUPPORTED, "unsupported slice size");
+    *bytes = request_bytes(H, W, S);
+    return PCS_OK;
+}
+
+pcs_status pcs_serve_fail_next_launch(pcs_server* sv, long long id) {
+    if (!sv) return pcs::set_last_error(PCS_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end()) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_fail_next_launch: unknown request");
+    it->second.fail_next = true;
+    return PCS_OK;
 }
 
 pcs_status pcs_serve_stats(pcs_server* sv, pcs_serve_summary* out) {
@@ -504,6 +641,7 @@ pcs_status pcs_serve_stats(pcs_server* sv, pcs_serve_summary* out) {
     out->span_s = sv->t_last_done;
     out->peak_inflight = sv->peak_inflight;
     out->peak_bytes = (double)sv->peak_bytes;
+    out->failed = sv->n_failed;
     std::vector<double> l = sv->latencies;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
@@ -525,11 +663,13 @@ void pcs_serve_stop(pcs_server* sv) {
     if (sv->worker.joinable()) sv->worker.join();
     for (auto& s : sv->slots) {
         if (s.stream) cudaStreamSynchronize(s.stream);
-        slot_release(s);
         if (s.stream) cudaStreamDestroy(s.stream);
     }
     for (auto& kv : sv->reqs)
-        for (auto& c : kv.second.chunks) cudaEventDestroy(c.done);
+        for (auto& c : kv.second.chunks)
+            if (c.done) cudaEventDestroy(c.done);
+    for (cudaEvent_t ev : sv->events) cudaEventDestroy(ev);
+    if (sv->arena_base) cudaFree(sv->arena_base);
     for (auto& kv : sv->sizes) {
         cudaFree(kv.second.dtab);
         cudaFree(kv.second.ddtab);

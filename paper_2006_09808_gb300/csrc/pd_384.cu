@@ -4,6 +4,7 @@
 namespace pcs {
 static const KernelEntry k_entries[] = {
     make_entry<Geo<384, 384, 4, 1>>(),
+    make_entry<Geo<384, 384, 4, 1, 384>>(),   // 12 warps per SM
 };
 const KernelEntry* entries_384(int* n) {
     *n = (int)(sizeof(k_entries) / sizeof(k_entries[0]));

@@ -47,14 +47,18 @@ def pinned(a):
     return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
 
 
-def _wait_all(sv, ids, timeout=120.0):
-    done, t0 = {}, time.time()
+def _wait_all(sv, ids, timeout=120.0, expect_ok=True):
+    done, status, t0 = {}, {}, time.time()
     while len(done) < len(ids):
-        for rid, lat in pcs.pcs_serve_poll(sv):
+        for rid, lat, st in pcs.pcs_serve_poll(sv):
             done[rid] = lat
+            status[rid] = st
         assert time.time() - t0 < timeout, "requests did not complete"
         time.sleep(0.002)
-    return done
+    if expect_ok:
+        assert all(v == pcs.PCS_OK for v in status.values()), status
+        return done
+    return done, status
 
 
 def _serve(sv, probs, chunks=3, gap_s=0.003):
@@ -123,13 +127,66 @@ def test_mix_equals_alone_and_plain():
 
 def test_budget_limits_admission():
     probs = _probs()[:3]
-    biggest = max(pb.voxels for pb in probs) * 25
-    sv = pcs.pcs_serve_start(hbm_budget_bytes=biggest + 1024, slots=4, n_iter=20, autotune=False)
+    need = [pcs.pcs_serve_request_bytes(pb.field.shape[1], pb.field.shape[2], pb.field.shape[0]) for pb in probs]
+    assert all(n >= 25 * pb.voxels for n, pb in zip(need, probs))  # field, mask, chi, four state arrays
+    # room for the biggest request alone, never for two of them
+    budget = max(need) + 1024
+    assert budget < min(a + b for k, a in enumerate(need) for b in need[k + 1:])
+    sv = pcs.pcs_serve_start(hbm_budget_bytes=budget, slots=4, n_iter=20, autotune=False)
     try:
         outs, _ = _serve(sv, probs)
         st = pcs.pcs_serve_stats(sv)
-        assert st["peak_inflight"] == 1 and st["peak_bytes"] <= biggest + 1024
+        assert st["peak_inflight"] == 1 and st["peak_bytes"] <= budget
         assert all(np.all(np.isfinite(o)) for o in outs)
+    finally:
+        pcs.pcs_serve_stop(sv)
+
+
+def test_serving_allocates_no_device_memory_while_it_runs():
+    """The budget is one arena allocated at start: serving requests of every size leaves the free
+    device memory unchanged (the scheduler thread never allocates)."""
+    probs = _probs()
+    sv = pcs.pcs_serve_start(hbm_budget_bytes=2 << 30, slots=3, n_iter=20, autotune=False)
+    try:
+        for H, *_ in PROBS:
+            pcs.pcs_serve_prepare_size(sv, H, H)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        outs, _ = _serve(sv, probs)
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
+        assert all(np.all(np.isfinite(o)) for o in outs)
+    finally:
+        pcs.pcs_serve_stop(sv)
+
+
+def test_failed_request_is_isolated():
+    """A launch failure injected on the host into one request finishes that request alone with an
+    error status; the requests around it complete with their correct chi, and the server keeps
+    serving."""
+    probs = [phantoms.volume(128, 128, 4, seed=21 + k, lam=5e-4, n_iter=N_ITER) for k in range(3)]
+    sv = pcs.pcs_serve_start(hbm_budget_bytes=1 << 30, slots=3, n_iter=N_ITER, autotune=False)
+    try:
+        L = pcs.pcs_serve_prepare_size(sv, 128, 128)["L"]
+        outs, keep, ids = [], [], []
+        for k, pb in enumerate(probs):
+            f, m = pinned(pb.field), pinned(pb.mask)
+            chi = pinned(np.full(pb.field.shape, np.nan, np.float32))
+            rid = pcs.pcs_serve_open(sv, 128, 128, 4, pb.lam, chi)
+            if k == 1:
+                pcs.pcs_serve_fail_next_launch(sv, rid)
+            keep += [f, m]
+            outs.append(chi)
+            ids.append(rid)
+            pcs.pcs_serve_push(sv, rid, 0, f, m)
+        _, status = _wait_all(sv, ids, expect_ok=False)
+        assert status[ids[1]] == pcs.PCS_ECUDA
+        assert status[ids[0]] == pcs.PCS_OK and status[ids[2]] == pcs.PCS_OK
+        st = pcs.pcs_serve_stats(sv)
+        assert st["failed"] == 1 and st["completed"] == 2
+        again, _ = _serve(sv, [probs[1]])  # the server goes on after the failure
+        for k, got in ((0, outs[0]), (2, outs[2]), (1, again[0])):
+            check_against_oracle(got, probs[k], L, k)
     finally:
         pcs.pcs_serve_stop(sv)
 
