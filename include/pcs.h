@@ -354,9 +354,10 @@ typedef struct pcs_tuning {
 
 /*
  * Create a batch solver: all slices of all volumes of a call are solved by the
- * fused primal-dual kernels -- one persistent launch per slice size, the
- * launches of the different sizes forked onto their own streams and joined
- * back into cuda_stream.  Step sizes are tau = sigma = 1/L(H, W), L the norm
+ * fused primal-dual kernels -- one persistent launch per slice size, run one
+ * size after another (the most work first; each launch balances its slices
+ * over every resident cluster), with the packing of every size's inputs
+ * forked onto per-size streams and everything joined back into cuda_stream.  Step sizes are tau = sigma = 1/L(H, W), L the norm
  * of the full-mask operator K (Sec. II.A pseudocode step 1), computed once per
  * size on the GPU.  autotune != 0: the first solve of a new slice size times
  * every compiled kernel variant of that size on that call's slice count

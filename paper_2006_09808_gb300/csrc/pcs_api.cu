@@ -784,6 +784,7 @@ struct pcs_batch {
         double L = 0.0;
         cudaStream_t stream = nullptr;
         cudaEvent_t done = nullptr;
+        cudaEvent_t solved = nullptr;  // the class's solve finished (the next class's solve may start)
         float* pk_field = nullptr;  // packed inputs / outputs [capacity][H][W]
         unsigned char* pk_mask = nullptr;
         float* pk_chi = nullptr;
@@ -810,6 +811,7 @@ void free_class(pcs_batch::Class& c) {
         if (q) cudaFree(q);
     if (c.stream) cudaStreamDestroy(c.stream);
     if (c.done) cudaEventDestroy(c.done);
+    if (c.solved) cudaEventDestroy(c.solved);
     c = pcs_batch::Class();
 }
 
@@ -882,6 +884,7 @@ pcs_status prepare_class(pcs_batch* b, pcs_batch::Class& c, int S) {
     if (!c.stream) {
         PCS_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "cudaStreamCreate");
         PCS_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming), "cudaEventCreate");
+        PCS_CUDA(cudaEventCreateWithFlags(&c.solved, cudaEventDisableTiming), "cudaEventCreate");
     }
     if (b->autotune && !c.tuned) {
         pcs_status st = tune_class(b, c, S < 128 ? S : 128, 40);
@@ -981,10 +984,19 @@ pcs_status pcs_batch_solve(pcs_batch* b, const pcs_volume* vols, int n_vols, int
         pcs_status st = prepare_class(b, b->classes[c], cls_S[c]);
         if (st != PCS_OK) return st;
     }
-    // fork: every class stream waits for the work already on the batch stream
+    // fork: every class stream waits for the work already on the batch stream and packs its
+    // inputs at once; the solves run one size class after another, the most work first (each
+    // persistent launch balances its slices over all resident clusters, so concurrent launches of
+    // different sizes would only contend for the SMs)
     PCS_CUDA(cudaEventRecord(b->fork, b->stream), "fork record");
-    for (size_t c = 0; c < b->classes.size(); ++c) {
-        if (cls_S[c] == 0) continue;
+    std::vector<size_t> order;
+    for (size_t c = 0; c < b->classes.size(); ++c)
+        if (cls_S[c] > 0) order.push_back(c);
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        return (double)cls_S[x] * b->classes[x].H * b->classes[x].W > (double)cls_S[y] * b->classes[y].H * b->classes[y].W;
+    });
+    const pcs_batch::Class* prev = nullptr;
+    for (size_t c : order) {
         pcs_batch::Class& C = b->classes[c];
         PCS_CUDA(cudaStreamWaitEvent(C.stream, b->fork, 0), "fork wait");
         const size_t sl = (size_t)C.H * C.W;
@@ -1000,8 +1012,11 @@ pcs_status pcs_batch_solve(pcs_batch* b, const pcs_volume* vols, int n_vols, int
             off += V.S;
         }
         PCS_CUDA(cudaMemcpyAsync(C.inv_den, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice, C.stream), "lambda upload");
+        if (prev) PCS_CUDA(cudaStreamWaitEvent(C.stream, prev->solved, 0), "wait for the previous class");
         pcs_status st = launch_solve(C.ctx, C.pk_field, C.pk_mask, cls_S[c], 1.0, tau, sigma, n_iter, C.pk_chi, C.inv_den);
         if (st != PCS_OK) return st;
+        PCS_CUDA(cudaEventRecord(C.solved, C.stream), "solved record");
+        prev = &C;
         off = 0;
         for (int v = 0; v < n_vols; ++v) {
             if (cls_of[v] != (int)c) continue;
