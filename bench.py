@@ -813,6 +813,7 @@ def run_uneven(args):
     def tuned_ctx(n, S):  # the variant the batch's autotuner chose for this size
         t = tun[n]
         return pcs.pcs_create(n, n, S, cluster_size=t["cluster_size"], kernel=t["kernel"], threads=t["threads"],
+                              tile=t["tile"],
                               stream=stream)
 
     ctxs = {n: tuned_ctx(n, max(sp["slices"] for sp in specs if sp["size"] == n)) for n in sizes}
@@ -887,7 +888,7 @@ def run_uneven(args):
                 "speedup_vs_per_volume": ms_volumes / ms_step,
                 "speedup_vs_per_slice": per_slice_ms / ms_step,
             },
-            "tuning": {str(n): {k: tun[n][k] for k in ("cluster_size", "kernel", "threads", "L")} for n in sizes},
+            "tuning": {str(n): {k: tun[n][k] for k in ("cluster_size", "kernel", "threads", "tile", "L")} for n in sizes},
             "clocks": clk.summary(),
         }
         if pool is not None:
@@ -993,7 +994,7 @@ def run_serve(args):
         if H not in ctxs:
             t = tun[H]
             ctxs[H] = pcs.pcs_create(H, H, 96, cluster_size=t["cluster_size"], kernel=t["kernel"],
-                                     threads=t["threads"])
+                                     threads=t["threads"], tile=t["tile"])
         f, m = pool[H]
         out = np.empty((S, H, H), np.float32)
         torch.cuda.synchronize()
@@ -1021,7 +1022,7 @@ def run_serve(args):
         "served": st,
         "per_request_plain_loop": {"value": vi_base / t_base, "unit": "voxel-iter/s",
                                    "requests": len(base_reqs), "note": "pcs_solve_slices_host, one after another"},
-        "tuning": {H: {k: tun[H][k] for k in ("cluster_size", "kernel", "threads", "L")} for H in sizes},
+        "tuning": {H: {k: tun[H][k] for k in ("cluster_size", "kernel", "threads", "tile", "L")} for H in sizes},
     }
     print(json.dumps(line), flush=True)
     return 0

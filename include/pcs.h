@@ -76,7 +76,9 @@ typedef struct pcs_options {
     int tv;            /* 0 = anisotropic TV: the dual TV prox clamps each gradient component
                           (the componentwise reading of Eq. (1)'s ||M G chi||_1, default);
                           1 = isotropic TV: it projects each pixel's (qx, qy) onto the unit disc */
-    int reserved[1];
+    int tile;          /* 0 = library default; else the FFT tile shape of a compiled variant:
+                          100 x (complex elements per lane of the row transforms) + those of the
+                          column transforms (e.g. 1616, 816, 1608) */
 } pcs_options;
 
 /* Diagnostics of one slice at (chi_N, p_N, q_N), in FP64 (see pcs_slice_report doc below). */
@@ -350,6 +352,9 @@ typedef struct pcs_tuning {
     double L;                          /* ||K||_2 of the full-mask operator; tau = sigma = 1/L */
     double ns_per_voxel_iter[8];       /* trial time of each candidate, in registry order */
     int cand_cluster_size[8], cand_kernel[8], cand_threads[8];
+    int tile;                          /* the chosen variant's FFT tile shape (see pcs_options.tile) */
+    int cand_tile[8];
+    int pad;
 } pcs_tuning;
 
 /*

@@ -39,7 +39,7 @@ class pcs_options(ctypes.Structure):
         ("threads", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("tv", ctypes.c_int),
-        ("reserved", ctypes.c_int * 1),
+        ("tile", ctypes.c_int),
     ]
 
 
@@ -83,16 +83,20 @@ class pcs_tuning(ctypes.Structure):
         ("cand_cluster_size", ctypes.c_int * 8),
         ("cand_kernel", ctypes.c_int * 8),
         ("cand_threads", ctypes.c_int * 8),
+        ("tile", ctypes.c_int),
+        ("cand_tile", ctypes.c_int * 8),
+        ("pad", ctypes.c_int),
     ]
 
     def as_dict(self):
         n = self.n_candidates
         return {
             "H": self.H, "W": self.W, "cluster_size": self.cluster_size, "kernel": self.kernel,
-            "threads": self.threads, "L": self.L,
+            "threads": self.threads, "tile": self.tile, "L": self.L,
             "candidates": [
                 {"cluster_size": self.cand_cluster_size[k], "kernel": self.cand_kernel[k],
-                 "threads": self.cand_threads[k], "ns_per_voxel_iter": self.ns_per_voxel_iter[k]}
+                 "threads": self.cand_threads[k], "tile": self.cand_tile[k],
+                 "ns_per_voxel_iter": self.ns_per_voxel_iter[k]}
                 for k in range(n)
             ],
         }
@@ -247,7 +251,7 @@ KERNEL_DEFAULT, KERNEL_STREAMING, KERNEL_RESIDENT = 0, 1, 2
 
 def pcs_create(H: int, W: int, max_slices: int, b0_axis: int = 0, cluster_size: int = 0, max_clusters: int = 0,
                kernel: int = KERNEL_DEFAULT, threads: int = 0, use_graph: bool = False, tv: int = 0,
-               stream=None):
+               stream=None, tile: int = 0):
     """Create a context; returns an opaque handle (c_void_p).  stream: torch.cuda.Stream or None (current)."""
     import torch
 
@@ -258,6 +262,7 @@ def pcs_create(H: int, W: int, max_slices: int, b0_axis: int = 0, cluster_size: 
     opt.threads = threads
     opt.use_graph = 1 if use_graph else 0
     opt.tv = tv
+    opt.tile = tile
     s = (stream or torch.cuda.current_stream()).cuda_stream
     h = ctypes.c_void_p()
     _check(lib.pcs_create(ctypes.byref(h), H, W, max_slices, ctypes.byref(opt), ctypes.c_void_p(s)), "pcs_create")

@@ -59,12 +59,13 @@ const std::vector<pcs::KernelEntry>& entries() {
     return v;
 }
 
-// First matching entry for (H, W) is the default; cluster_size > 0 and
-// kernel (1 streaming, 2 resident) narrow the choice.
-const pcs::KernelEntry* find_entry(int H, int W, int cluster_size, int kernel = 0, int threads = 0) {
+// First matching entry for (H, W) is the default; cluster_size > 0, kernel
+// (1 streaming, 2 resident), threads and tile narrow the choice.
+const pcs::KernelEntry* find_entry(int H, int W, int cluster_size, int kernel = 0, int threads = 0, int tile = 0) {
     for (const auto& e : entries())
         if (e.H == H && e.W == W && (cluster_size <= 0 || e.C == cluster_size) &&
-            (kernel <= 0 || e.resident == (kernel == 2 ? 1 : 0)) && (threads <= 0 || e.threads == threads))
+            (kernel <= 0 || e.resident == (kernel == 2 ? 1 : 0)) && (threads <= 0 || e.threads == threads) &&
+            (tile <= 0 || e.tile == tile))
             return &e;
     return nullptr;
 }
@@ -517,12 +518,12 @@ pcs_status pcs_create(pcs_ctx** out, int H, int W, int max_slices, const pcs_opt
     if (o.tv != 0 && o.tv != 1) return fail(PCS_EINVAL, "tv must be 0 (anisotropic) or 1 (isotropic)");
     if (o.use_graph && cuda_stream == nullptr)
         return fail(PCS_EINVAL, "use_graph needs a non-NULL stream (the legacy stream cannot be captured)");
-    const pcs::KernelEntry* entry = find_entry(H, W, o.cluster_size, o.kernel, o.threads);
+    const pcs::KernelEntry* entry = find_entry(H, W, o.cluster_size, o.kernel, o.threads, o.tile);
     const bool any_size = !entry && find_entry(H, W, 0) == nullptr && o.cluster_size == 0 && o.kernel == 0 &&
-                          o.threads == 0 && pcs::gen_supported(H, W);
+                          o.threads == 0 && o.tile == 0 && pcs::gen_supported(H, W);
     if (!entry && !any_size)
-        return fail(PCS_EUNSUPPORTED, "no kernel for %d x %d slices with cluster_size %d, kernel %d, threads %d", H,
-                    W, o.cluster_size, o.kernel, o.threads);
+        return fail(PCS_EUNSUPPORTED, "no kernel for %d x %d slices with cluster_size %d, kernel %d, threads %d, tile %d",
+                    H, W, o.cluster_size, o.kernel, o.threads, o.tile);
 
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -841,6 +842,7 @@ pcs_status tune_class(pcs_batch* b, pcs_batch::Class& c, int S, int trial_iters)
         o.cluster_size = e.C;
         o.kernel = e.resident ? 2 : 1;
         o.threads = e.threads;
+        o.tile = e.tile;
         o.use_graph = 0;
         pcs_ctx* tc = nullptr;
         st = pcs_create(&tc, c.H, c.W, S, &o, c.stream);
@@ -861,11 +863,13 @@ pcs_status tune_class(pcs_batch* b, pcs_batch::Class& c, int S, int trial_iters)
         t.cand_cluster_size[k] = e.C;
         t.cand_kernel[k] = e.resident ? 2 : 1;
         t.cand_threads[k] = e.threads;
+        t.cand_tile[k] = e.tile;
         if (t.ns_per_voxel_iter[k] < best) {
             best = t.ns_per_voxel_iter[k];
             t.cluster_size = e.C;
             t.kernel = e.resident ? 2 : 1;
             t.threads = e.threads;
+            t.tile = e.tile;
         }
     }
     cudaEventDestroy(e0);
@@ -907,6 +911,7 @@ pcs_status prepare_class(pcs_batch* b, pcs_batch::Class& c, int S) {
         o.cluster_size = c.tuning.cluster_size;
         o.kernel = c.tuning.kernel;
         o.threads = c.tuning.threads;
+        o.tile = c.tuning.tile;
     }
     pcs_status st = pcs_create(&c.ctx, c.H, c.W, cap, &o, c.stream);
     if (st != PCS_OK) return st;
@@ -1042,6 +1047,7 @@ pcs_status pcs_batch_tuning(pcs_batch* b, int H, int W, pcs_tuning* out) {
                 out->cluster_size = e ? e->C : 0;
                 out->kernel = e ? (e->resident ? 2 : 1) : 0;
                 out->threads = e ? e->threads : 0;
+                out->tile = e ? e->tile : 0;
                 out->L = c.L;
                 return PCS_OK;
             }

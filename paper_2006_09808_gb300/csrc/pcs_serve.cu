@@ -67,7 +67,7 @@ double seconds_since(Clock::time_point t0) {
     return std::chrono::duration<double>(Clock::now() - t0).count();
 }
 
-const pcs::KernelEntry* registry_find(int H, int W, int C, int kernel, int threads) {
+const pcs::KernelEntry* registry_find(int H, int W, int C, int kernel, int threads, int tile = 0) {
     const pcs::KernelEntry* (*fns[])(int*) = {pcs::entries_64,  pcs::entries_128, pcs::entries_192,
                                                pcs::entries_256, pcs::entries_384, pcs::entries_512};
     for (auto fn : fns) {
@@ -75,7 +75,8 @@ const pcs::KernelEntry* registry_find(int H, int W, int C, int kernel, int threa
         const pcs::KernelEntry* e = fn(&n);
         for (int k = 0; k < n; ++k)
             if (e[k].H == H && e[k].W == W && (C <= 0 || e[k].C == C) &&
-                (kernel <= 0 || e[k].resident == (kernel == 2 ? 1 : 0)) && (threads <= 0 || e[k].threads == threads))
+                (kernel <= 0 || e[k].resident == (kernel == 2 ? 1 : 0)) && (threads <= 0 || e[k].threads == threads) &&
+                (tile <= 0 || e[k].tile == tile))
                 return &e[k];
     }
     return nullptr;
@@ -277,7 +278,7 @@ pcs_status size_setup(pcs_server* sv, int H, int W, SizeInfo** out) {
     cudaStreamDestroy(ts);
     if (st != PCS_OK) return st;
     si.L = si.tuning.L;
-    si.entry = registry_find(H, W, si.tuning.cluster_size, si.tuning.kernel, si.tuning.threads);
+    si.entry = registry_find(H, W, si.tuning.cluster_size, si.tuning.kernel, si.tuning.threads, si.tuning.tile);
     if (!si.entry && pcs::gen_supported(H, W)) {
         if (!(si.L > 0.0) || pcs::gen_create(&si.gen, H, W, 1, sv->cfg.b0_axis, 0) != cudaSuccess)
             return pcs::set_last_error(PCS_ECUDA, "serve: any-size set-up");

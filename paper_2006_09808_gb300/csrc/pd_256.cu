@@ -12,6 +12,10 @@ static const KernelEntry k_entries[] = {
     make_entry<Geo<256, 256, 8, 2>>(),
     // eight elements per lane, 512-thread CTAs (more warps per SM)
     make_resident_entry<GeoRes<256, 256, 8, 512, 8, 8>>(),
+    // other FFT tile shapes of the default geometry (the autotuner's choice): rows with 8
+    // elements per lane (16 lanes per row, two row passes), or columns with 8 (32 lanes per column)
+    make_entry<Geo<256, 256, 4, 1, 512, 8, 16>>(),
+    make_entry<Geo<256, 256, 4, 1, 512, 16, 8>>(),
 };
 const KernelEntry* entries_256(int* n) {
     *n = (int)(sizeof(k_entries) / sizeof(k_entries[0]));

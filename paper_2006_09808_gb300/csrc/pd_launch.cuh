@@ -16,6 +16,7 @@ struct KernelEntry {
     int resident;  // 1: state held on chip (pd_resident_kernel); 0: state streamed (pd_cluster_kernel)
     size_t smem;
     int threads;
+    int tile;      // FFT tile shape: 100 x (elements per lane of the row transforms) + those of the columns
     // Sets function attributes; returns how many clusters of the iteration
     // kernel and of the auxiliary kernels can be resident.
     cudaError_t (*prepare)(int* max_clusters, int* max_clusters_aux);
@@ -103,7 +104,7 @@ cudaError_t prepare_all(int* max_clusters, int* max_clusters_aux) {
 template <class G>
 constexpr KernelEntry make_entry() {
     return KernelEntry{G::H,           G::W,           G::C,       0,
-                       G::SMEM_BYTES,  G::NT,          &prepare_all<G>,
+                       G::SMEM_BYTES,  G::NT,          100 * G::ER + G::EC, &prepare_all<G>,
                        &launch_pd<G>,  &launch_report<G>, &launch_opnorm<G>, &launch_pd_sched<G>};
 }
 
@@ -128,7 +129,7 @@ template <class GR>
 constexpr KernelEntry make_resident_entry() {
     using G = typename GR::B;
     return KernelEntry{GR::H,           GR::W,          GR::C,       1,
-                       GR::SMEM_BYTES,  GR::NT,         &prepare_res<GR>,
+                       GR::SMEM_BYTES,  GR::NT,         100 * GR::ER + GR::EC, &prepare_res<GR>,
                        &launch_res<GR>, &launch_report<G>, &launch_opnorm<G>, nullptr};
 }
 

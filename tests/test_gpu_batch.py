@@ -72,7 +72,8 @@ def test_batch_matches_per_volume_solves():
         m = torch.from_numpy(pb.mask).cuda()
         chi = torch.empty_like(f)
         t = tun[H]
-        ctx = pcs.pcs_create(H, W, S, cluster_size=t["cluster_size"], kernel=t["kernel"], threads=t["threads"])
+        ctx = pcs.pcs_create(H, W, S, cluster_size=t["cluster_size"], kernel=t["kernel"], threads=t["threads"],
+                             tile=t["tile"])
         try:
             pcs.pcs_solve_slices(ctx, f, m, pb.lam, 1.0 / L, 1.0 / L, 60, chi)
             torch.cuda.synchronize()

@@ -116,7 +116,8 @@ def test_mix_equals_alone_and_plain():
         f = torch.from_numpy(pb.field).cuda()
         m = torch.from_numpy(pb.mask).cuda()
         chi = torch.empty_like(f)
-        ctx = pcs.pcs_create(H, W, S, cluster_size=t["cluster_size"], kernel=t["kernel"], threads=t["threads"])
+        ctx = pcs.pcs_create(H, W, S, cluster_size=t["cluster_size"], kernel=t["kernel"], threads=t["threads"],
+                             tile=t["tile"])
         try:
             pcs.pcs_solve_slices(ctx, f, m, pb.lam, 1 / t["L"], 1 / t["L"], N_ITER, chi)
             torch.cuda.synchronize()
