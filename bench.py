@@ -54,11 +54,12 @@ def dist_env():
 
 
 def kernel_source_hash():
-    """Hash of the iteration kernel's sources, ignoring // comments and blank lines (a comment
-    edit does not change the kernel the ncu counters were taken from)."""
+    """Hash of the iteration kernel's device code (the FFT engine and the fused kernel), ignoring
+    // comments and blank lines (a comment edit does not change the kernel the ncu counters were
+    taken from); the variant table and launch glue are host code."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2006_09808_gb300", "csrc")
-    for name in ("fft_core.cuh", "pd_cluster.cuh", "pd_launch.cuh", "pd_256.cu"):  # the iteration kernel's files
+    for name in ("fft_core.cuh", "pd_cluster.cuh"):  # the iteration kernel's device code
         for line in open(os.path.join(csrc, name), encoding="utf-8"):
             code = line.split("//", 1)[0].rstrip()
             if code:
