@@ -536,8 +536,10 @@ def run_volume3d(args):
             "config": {"workload": "3-D: the 256x256x64 volume as one unknown (3-D G and D, B0 along z), "
                                    "500 PD iterations, lambda=5e-4", "H": H, "W": W, "slices": SLICES,
                        "n_iter": N_ITER, "tau_sigma": STEP_3D, "l2": "flushed between steps (256 MiB device write)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "roofline": {"bound": "latency (L2)", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None,
+                         "frac_of": "the measured HBM copy peak, in useful bytes (state, inputs and the half "
+                                    "spectrum's four passes per convolution)",
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "alg_bytes_per_voxel_iter": ALG_BYTES_3D},
             "e2e": {"value": work / (sum(e2e) / len(e2e)), "unit": "voxel-iter/s",
@@ -639,8 +641,9 @@ def run_native_shape(args):
                                    "2*3*43), 500 PD iterations, lambda=5e-4", "H": NATIVE_H, "W": NATIVE_W,
                        "slices": NATIVE_S, "n_iter": N_ITER, "tau_sigma": STEP_2D_SAFE,
                        "l2": "flushed between steps (256 MiB device write)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "roofline": {"bound": "latency (L2)", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None,
+                         "frac_of": "the measured HBM copy peak, in useful bytes (37 B per voxel-iteration)",
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "alg_bytes_per_voxel_iter": ALG_BYTES_PER_VOXEL_ITER},
             "e2e": {"value": work / (sum(e2e) / len(e2e)), "unit": "voxel-iter/s",
@@ -939,7 +942,7 @@ def run_serve(args):
     torch.cuda.set_device(0)
     pcs.load_library()
     n_iter = 400
-    reqs = phantoms.config5_arrivals(args.requests, rate_hz=40.0, seed=0)
+    reqs = phantoms.config5_arrivals(args.requests, rate_hz=args.rate, seed=0)
     sizes = sorted({r["size"] for r in reqs})
     # one pinned pool volume per size (96 slices); a request takes its first S slices
     pool = {}
@@ -988,6 +991,8 @@ def run_serve(args):
     window = reqs[-1]["t"] - reqs[0]["t"]
     # baseline: the same requests solved one after another with plain per-request calls
     base_reqs = reqs[: args.baseline_requests] if args.baseline_requests > 0 else reqs
+    if args.no_baseline:
+        base_reqs = []
     ctxs = {}
     t_base, vi_base = 0.0, 0.0
     for r in base_reqs:
@@ -1015,14 +1020,15 @@ def run_serve(args):
         "higher_is_better": True,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"serving: {len(reqs)} Poisson arrivals at 40 volumes/s of uneven-batch-style "
-                               "volumes (128..512^2, 16-96 slices, 400 iterations), slices released over 100 ms, "
-                               "120 GB budget", "slots": args.slots},
+        "config": {"workload": f"serving: {len(reqs)} Poisson arrivals at {args.rate:g} volumes/s of uneven-batch-"
+                               "style volumes (128..512^2, 16-96 slices, 400 iterations), slices released over "
+                               "100 ms, 120 GB budget", "slots": args.slots, "rate_hz": args.rate},
         "latency_s": {"p50": st["p50_s"], "p99": st["p99_s"], "max": st["max_s"]},
         "offered_voxel_iter_per_s": vox_iters / max(window, 1e-9),
         "served": st,
-        "per_request_plain_loop": {"value": vi_base / t_base, "unit": "voxel-iter/s",
-                                   "requests": len(base_reqs), "note": "pcs_solve_slices_host, one after another"},
+        "per_request_plain_loop": None if not base_reqs else {
+            "value": vi_base / t_base, "unit": "voxel-iter/s", "requests": len(base_reqs),
+            "note": "pcs_solve_slices_host, one after another"},
         "tuning": {H: {k: tun[H][k] for k in ("cluster_size", "kernel", "threads", "tile", "L")} for H in sizes},
     }
     print(json.dumps(line), flush=True)
@@ -1050,6 +1056,8 @@ def main():
                          "native: the any-size path on 25 slices of 256x258; uneven: the 48-volume uneven batch")
     ap.add_argument("--requests", type=int, default=400, help="serving: number of requests (the 400-request window)")
     ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight")
+    ap.add_argument("--rate", type=float, default=40.0, help="serving: mean arrivals per second (Poisson)")
+    ap.add_argument("--no-baseline", action="store_true", help="serving: skip the per-request baseline")
     ap.add_argument("--baseline-requests", type=int, default=0,
                     help="serving: requests in the per-request baseline (0: all of them)")
     args = ap.parse_args()

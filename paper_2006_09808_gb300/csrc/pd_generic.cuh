@@ -184,7 +184,9 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
                 float2 A0 = b[j0], B0 = make_float2(0.f, 0.f);
                 float2 A1 = b[j1], B1 = make_float2(0.f, 0.f);
                 int m0 = 0, m1 = 0;
-#pragma unroll 1
+                // unrolled: the next terms' shared-memory loads overlap this term's FMAs (the
+                // accumulation order is unchanged)
+#pragma unroll 3
                 for (int q = 1; q <= h; ++q) {
                     m0 += qp0;
                     if (m0 >= r) m0 -= r;
@@ -271,63 +273,125 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
     float* __restrict__ pp = g.p;
     float* __restrict__ qxp = g.qx;
     float* __restrict__ qyp = g.qy;
+    // Each lane takes adjacent column pairs (n, n+1) of both rows with 8-byte accesses (W is
+    // even, so every pair starts on an 8-byte boundary); the neighbouring column on the other
+    // side of a pair is the adjacent lane's, passed by shuffle (lanes 0 and 31 of a chunk load
+    // it).  Same arithmetic per element as one column at a time.
+    const int NP = W / 2;
     if (g.phase == 0) {
         // dual step at both rows (Sec. II.A): p and q from u = D chibar and chibar's differences
         const bool down1 = (i1 + 1 < H);
         const float inv_den = g.inv_den_slice ? __ldg(g.inv_den_slice + s) : g.inv_den;
-#pragma unroll 3
-        for (int n = lane; n < W; n += 32) {
-            const float2 uv = u[n];
-            const bool right = (n + 1 < W);
+#pragma unroll 2
+        for (int m0 = 0; m0 < NP; m0 += 32) {
+            const int m = m0 + lane;
+            const bool act = m < NP;
+            const int n = 2 * (act ? m : NP - 1);  // inactive lanes shadow the last pair (no stores)
             const size_t a0 = r0 + n, a1 = r1 + n;
-            const float c0 = __ldcg(cbar + a0), c1 = __ldcg(cbar + a1);
-            const float c0r = right ? __ldcg(cbar + a0 + 1) : c0;
-            const float c1r = right ? __ldcg(cbar + a1 + 1) : c1;
-            const float c2 = down1 ? __ldcg(cbar + a1 + W) : c1;
-            const float m0 = (float)__ldg(msk + a0), m1 = (float)__ldg(msk + a1);
-            const float w0 = wgt ? __ldg(wgt + a0) : m0;
-            const float w1 = wgt ? __ldg(wgt + a1) : m1;
-            const float p0 = (__ldcg(pp + a0) + sigma * (w0 * (uv.x - __ldg(fld + a0)))) * inv_den;
-            const float p1 = (__ldcg(pp + a1) + sigma * (w1 * (uv.y - __ldg(fld + a1)))) * inv_den;
-            float qx0 = __ldcg(qxp + a0) + sigma * m0 * (c0r - c0);
-            float qy0 = __ldcg(qyp + a0) + sigma * m0 * (c1 - c0);
-            float qx1 = __ldcg(qxp + a1) + sigma * m1 * (c1r - c1);
-            float qy1 = __ldcg(qyp + a1) + sigma * m1 * (c2 - c1);
-            tv_prox(qx0, qy0, g.tv_iso);
-            tv_prox(qx1, qy1, g.tv_iso);
-            __stcg(pp + a0, p0);
-            __stcg(pp + a1, p1);
-            __stcg(qxp + a0, qx0);
-            __stcg(qyp + a0, qy0);
-            __stcg(qxp + a1, qx1);
-            __stcg(qyp + a1, qy1);
-            o[n] = make_float2(w0 * p0, w1 * p1);  // W p, transformed next
+            const float4 uv = *reinterpret_cast<const float4*>(u + n);  // u[n], u[n+1]
+            const float2 c0 = __ldcg(reinterpret_cast<const float2*>(cbar + a0));
+            const float2 c1 = __ldcg(reinterpret_cast<const float2*>(cbar + a1));
+            float c0r = __shfl_down_sync(0xffffffffu, c0.x, 1);  // column n+2 of row i0
+            float c1r = __shfl_down_sync(0xffffffffu, c1.x, 1);
+            if (n + 2 >= W) {  // past the last column the difference is zero (Neumann)
+                c0r = c0.y;
+                c1r = c1.y;
+            } else if (lane == 31 || m + 1 >= NP) {
+                c0r = __ldcg(cbar + a0 + 2);
+                c1r = __ldcg(cbar + a1 + 2);
+            }
+            const float2 c2 = down1 ? __ldcg(reinterpret_cast<const float2*>(cbar + a1 + W)) : c1;
+            const uchar2 mk0 = __ldg(reinterpret_cast<const uchar2*>(msk + a0));
+            const uchar2 mk1 = __ldg(reinterpret_cast<const uchar2*>(msk + a1));
+            const float m00 = (float)mk0.x, m01 = (float)mk0.y, m10 = (float)mk1.x, m11 = (float)mk1.y;
+            float2 w0 = make_float2(m00, m01), w1 = make_float2(m10, m11);
+            if (wgt) {
+                w0 = __ldg(reinterpret_cast<const float2*>(wgt + a0));
+                w1 = __ldg(reinterpret_cast<const float2*>(wgt + a1));
+            }
+            const float2 f0 = __ldg(reinterpret_cast<const float2*>(fld + a0));
+            const float2 f1 = __ldg(reinterpret_cast<const float2*>(fld + a1));
+            const float2 pa = __ldcg(reinterpret_cast<const float2*>(pp + a0));
+            const float2 pb = __ldcg(reinterpret_cast<const float2*>(pp + a1));
+            const float2 qxa = __ldcg(reinterpret_cast<const float2*>(qxp + a0));
+            const float2 qxb = __ldcg(reinterpret_cast<const float2*>(qxp + a1));
+            const float2 qya = __ldcg(reinterpret_cast<const float2*>(qyp + a0));
+            const float2 qyb = __ldcg(reinterpret_cast<const float2*>(qyp + a1));
+            // column n: (row i0, row i1) = (uv.x, uv.y); column n+1: (uv.z, uv.w)
+            const float p00 = (pa.x + sigma * (w0.x * (uv.x - f0.x))) * inv_den;
+            const float p10 = (pb.x + sigma * (w1.x * (uv.y - f1.x))) * inv_den;
+            const float p01 = (pa.y + sigma * (w0.y * (uv.z - f0.y))) * inv_den;
+            const float p11 = (pb.y + sigma * (w1.y * (uv.w - f1.y))) * inv_den;
+            float qx00 = qxa.x + sigma * m00 * (c0.y - c0.x);
+            float qy00 = qya.x + sigma * m00 * (c1.x - c0.x);
+            float qx10 = qxb.x + sigma * m10 * (c1.y - c1.x);
+            float qy10 = qyb.x + sigma * m10 * (c2.x - c1.x);
+            float qx01 = qxa.y + sigma * m01 * (c0r - c0.y);
+            float qy01 = qya.y + sigma * m01 * (c1.y - c0.y);
+            float qx11 = qxb.y + sigma * m11 * (c1r - c1.y);
+            float qy11 = qyb.y + sigma * m11 * (c2.y - c1.y);
+            tv_prox(qx00, qy00, g.tv_iso);
+            tv_prox(qx10, qy10, g.tv_iso);
+            tv_prox(qx01, qy01, g.tv_iso);
+            tv_prox(qx11, qy11, g.tv_iso);
+            if (act) {
+                __stcg(reinterpret_cast<float2*>(pp + a0), make_float2(p00, p01));
+                __stcg(reinterpret_cast<float2*>(pp + a1), make_float2(p10, p11));
+                __stcg(reinterpret_cast<float2*>(qxp + a0), make_float2(qx00, qx01));
+                __stcg(reinterpret_cast<float2*>(qyp + a0), make_float2(qy00, qy01));
+                __stcg(reinterpret_cast<float2*>(qxp + a1), make_float2(qx10, qx11));
+                __stcg(reinterpret_cast<float2*>(qyp + a1), make_float2(qy10, qy11));
+                // W p, transformed next
+                *reinterpret_cast<float4*>(o + n) = make_float4(w0.x * p00, w1.x * p10, w0.y * p01, w1.y * p11);
+            }
         }
     } else {
         // primal step: chi+ = chi - tau (v + G^T q), v = D W p; chibar = 2 chi+ - chi.
         // q is zero wherever the 0/1 mask is (zero start, masked increments), so M q = q.
         const bool up0 = (i0 > 0), down1 = (i1 + 1 < H);
-#pragma unroll 3
-        for (int n = lane; n < W; n += 32) {
-            const float2 vv = u[n];
+#pragma unroll 2
+        for (int m0 = 0; m0 < NP; m0 += 32) {
+            const int m = m0 + lane;
+            const bool act = m < NP;
+            const int n = 2 * (act ? m : NP - 1);
             const size_t a0 = r0 + n, a1 = r1 + n;
-            const float qx0 = __ldcg(qxp + a0), qx1 = __ldcg(qxp + a1);
-            const float qy0 = __ldcg(qyp + a0), qy1 = __ldcg(qyp + a1);
-            const float qxl0 = (n > 0) ? __ldcg(qxp + a0 - 1) : 0.f;
-            const float qxl1 = (n > 0) ? __ldcg(qxp + a1 - 1) : 0.f;
-            const float qyu0 = up0 ? __ldcg(qyp + a0 - W) : 0.f;
-            const bool last_col = (n + 1 == W);
-            const float d0 = (qxl0 - (last_col ? 0.f : qx0)) + (qyu0 - qy0);  // row i0 < H - 1
-            const float d1 = (qxl1 - (last_col ? 0.f : qx1)) + (qy0 - (down1 ? qy1 : 0.f));
-            const float c0 = __ldcg(chi + a0), c1 = __ldcg(chi + a1);
-            const float n0 = c0 - tau * vv.x - tau * d0;
-            const float n1 = c1 - tau * vv.y - tau * d1;
-            __stcg(chi + a0, n0);
-            __stcg(chi + a1, n1);
-            const float b0 = 2.f * n0 - c0, b1 = 2.f * n1 - c1;
-            __stcg(cbar + a0, b0);
-            __stcg(cbar + a1, b1);
-            o[n] = make_float2(b0, b1);
+            const float4 vv = *reinterpret_cast<const float4*>(u + n);
+            const float2 qxa = __ldcg(reinterpret_cast<const float2*>(qxp + a0));
+            const float2 qxb = __ldcg(reinterpret_cast<const float2*>(qxp + a1));
+            const float2 qya = __ldcg(reinterpret_cast<const float2*>(qyp + a0));
+            const float2 qyb = __ldcg(reinterpret_cast<const float2*>(qyp + a1));
+            float qxl0 = __shfl_up_sync(0xffffffffu, qxa.y, 1);  // column n-1
+            float qxl1 = __shfl_up_sync(0xffffffffu, qxb.y, 1);
+            if (n == 0) {
+                qxl0 = 0.f;
+                qxl1 = 0.f;
+            } else if (lane == 0) {
+                qxl0 = __ldcg(qxp + a0 - 1);
+                qxl1 = __ldcg(qxp + a1 - 1);
+            }
+            const float2 qyu = up0 ? __ldcg(reinterpret_cast<const float2*>(qyp + a0 - W)) : make_float2(0.f, 0.f);
+            const bool last_col = (n + 2 == W);  // column n+1 is the last
+            // column n (never the last: n <= W - 2)
+            const float d00 = (qxl0 - qxa.x) + (qyu.x - qya.x);
+            const float d10 = (qxl1 - qxb.x) + (qya.x - (down1 ? qyb.x : 0.f));
+            // column n+1
+            const float d01 = (qxa.x - (last_col ? 0.f : qxa.y)) + (qyu.y - qya.y);
+            const float d11 = (qxb.x - (last_col ? 0.f : qxb.y)) + (qya.y - (down1 ? qyb.y : 0.f));
+            const float2 ca = __ldcg(reinterpret_cast<const float2*>(chi + a0));
+            const float2 cb2 = __ldcg(reinterpret_cast<const float2*>(chi + a1));
+            const float n00 = ca.x - tau * vv.x - tau * d00;
+            const float n10 = cb2.x - tau * vv.y - tau * d10;
+            const float n01 = ca.y - tau * vv.z - tau * d01;
+            const float n11 = cb2.y - tau * vv.w - tau * d11;
+            const float b00 = 2.f * n00 - ca.x, b10 = 2.f * n10 - cb2.x;
+            const float b01 = 2.f * n01 - ca.y, b11 = 2.f * n11 - cb2.y;
+            if (act) {
+                __stcg(reinterpret_cast<float2*>(chi + a0), make_float2(n00, n01));
+                __stcg(reinterpret_cast<float2*>(chi + a1), make_float2(n10, n11));
+                __stcg(reinterpret_cast<float2*>(cbar + a0), make_float2(b00, b01));
+                __stcg(reinterpret_cast<float2*>(cbar + a1), make_float2(b10, b11));
+                *reinterpret_cast<float4*>(o + n) = make_float4(b00, b10, b01, b11);
+            }
         }
     }
     __syncwarp();

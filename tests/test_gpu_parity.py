@@ -388,3 +388,28 @@ def test_host_buffer_entry_point_matches_device_path():
     finally:
         pcs.pcs_destroy(ctx)
     assert np.array_equal(out, dev)
+
+
+@pytest.mark.parametrize("H", [64, 128, 192, 256, 384, 512])
+def test_every_compiled_variant_matches_the_oracle(H):
+    """Every compiled variant of a slice size (cluster shape, kernel kind, threads per CTA, FFT
+    tile shape), listed by the autotuner's candidate record, against the FP64 oracle."""
+    pb = phantoms.volume(H, H, 2, seed=40 + H, lam=5e-4, n_iter=60)
+    batch = pcs.pcs_batch_create(autotune=True)
+    try:
+        f = torch.from_numpy(pb.field).cuda()
+        m = torch.from_numpy(pb.mask).cuda()
+        pcs.pcs_batch_solve(batch, [(f, m, pb.lam, torch.empty_like(f))], 2)
+        pcs.pcs_batch_check(batch)
+        cands = pcs.pcs_batch_tuning(batch, H, H)["candidates"]
+    finally:
+        pcs.pcs_batch_destroy(batch)
+    assert len(cands) >= 1
+    L, tau, sigma = steps(H, H)
+    ref = oracle_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter)
+    for c in cands:
+        got = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, cluster_size=c["cluster_size"],
+                        kernel=c["kernel"], threads=c["threads"], tile=c["tile"])
+        assert np.all(np.isfinite(got)), c
+        for s in range(2):
+            assert rel_l2(got[s], ref[s]) <= TOL, (c, s)
