@@ -468,6 +468,17 @@ PCS_API pcs_status pcs_serve_push(pcs_server *sv, long long id, int s0, int n, c
 PCS_API pcs_status pcs_serve_poll(pcs_server *sv, long long *ids, double *latency_s, pcs_status *status, int max,
                                   int *n_out);
 
+/*
+ * The serving arena's placement on the host, for inspection and tests (no GPU):
+ * an arena of `capacity` bytes replays ops[0..n_ops): ops[k] > 0 allocates that
+ * many bytes (rounded up to 256) first fit; ops[k] < 0 releases the range that
+ * op -ops[k]-1 allocated (nothing if that allocation was refused; PCS_EINVAL if
+ * that op is not an earlier allocation).  offsets[k] receives op k's offset (-1 if it did not
+ * fit or was a release); used_after[k] (may be NULL) the bytes in use after it.
+ */
+PCS_API pcs_status pcs_serve_arena_plan(size_t capacity, const long long *ops, int n_ops, long long *offsets,
+                                        size_t *used_after);
+
 /* Device bytes one request of S slices of H x W holds while admitted (its share of the budget). */
 PCS_API pcs_status pcs_serve_request_bytes(int H, int W, int S, size_t *bytes);
 

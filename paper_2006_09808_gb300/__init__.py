@@ -184,6 +184,8 @@ def load_library(path: str = LIB_PATH):
         "pcs_serve_poll": (i, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d), ctypes.POINTER(i), i,
                                ctypes.POINTER(i)]),
         "pcs_serve_request_bytes": (i, [i, i, i, ctypes.POINTER(ctypes.c_size_t)]),
+        "pcs_serve_arena_plan": (i, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_longlong), i,
+                                     ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_size_t)]),
         "pcs_serve_fail_next_launch": (i, [vp, ctypes.c_longlong]),
         "pcs_serve_stats": (i, [vp, ctypes.POINTER(pcs_serve_summary)]),
         "pcs_serve_stop": (None, [vp]),
@@ -562,6 +564,17 @@ def pcs_serve_poll(server, max_items: int = 256):
     n = ctypes.c_int()
     _check(load_library().pcs_serve_poll(server, ids, lat, st, max_items, ctypes.byref(n)), "pcs_serve_poll")
     return [(ids[k], lat[k], st[k]) for k in range(n.value)]
+
+
+def pcs_serve_arena_plan(capacity: int, ops):
+    """Replay allocate (> 0 bytes) / release (-(k+1): the range of op k) ops on the serving arena's
+    host-side placement; returns (offsets, bytes in use after each op)."""
+    n = len(ops)
+    arr = (ctypes.c_longlong * max(1, n))(*ops)
+    off = (ctypes.c_longlong * max(1, n))()
+    used = (ctypes.c_size_t * max(1, n))()
+    _check(load_library().pcs_serve_arena_plan(capacity, arr, n, off, used), "pcs_serve_arena_plan")
+    return list(off)[:n], list(used)[:n]
 
 
 def pcs_serve_request_bytes(H: int, W: int, S: int) -> int:

@@ -616,6 +616,36 @@ pcs_status pcs_serve_poll(pcs_server* sv, long long* ids, double* latency_s, pcs
     return PCS_OK;
 }
 
+pcs_status pcs_serve_arena_plan(size_t capacity, const long long* ops, int n_ops, long long* offsets,
+                                size_t* used_after) {
+    if (!ops || !offsets || n_ops < 0) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_arena_plan: bad argument");
+    Arena a;
+    const size_t cap = capacity / Arena::kAlign * Arena::kAlign;
+    a.reset(cap);
+    std::vector<std::pair<size_t, size_t>> held(n_ops, {SIZE_MAX, 0});  // by op index: (offset, bytes)
+    for (int k = 0; k < n_ops; ++k) {
+        offsets[k] = -1;
+        if (ops[k] > 0) {  // allocate ops[k] bytes (rounded up to the alignment)
+            const size_t b = align_up((size_t)ops[k]);
+            const size_t off = a.alloc(b);
+            if (off != SIZE_MAX) {
+                held[k] = {off, b};
+                offsets[k] = (long long)off;
+            }
+        } else if (ops[k] < 0) {  // release the range allocated by op -ops[k] - 1
+            const long long j = -ops[k] - 1;
+            if (j >= k || ops[j] <= 0)
+                return pcs::set_last_error(PCS_EINVAL, "pcs_serve_arena_plan: release of an op that allocated nothing");
+            if (held[j].first != SIZE_MAX) {  // a refused (or already released) allocation: nothing to do
+                a.release(held[j].first, held[j].second);
+                held[j] = {SIZE_MAX, 0};
+            }
+        }
+        if (used_after) used_after[k] = a.used();
+    }
+    return PCS_OK;
+}
+
 pcs_status pcs_serve_request_bytes(int H, int W, int S, size_t* bytes) {
     if (!bytes || S < 1) return pcs::set_last_error(PCS_EINVAL, "pcs_serve_request_bytes: bad argument");
     if (!served_size(H, W)) return pcs::set_last_error(PCS_EUNSUPPORTED, "unsupported slice size");
