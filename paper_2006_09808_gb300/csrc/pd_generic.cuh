@@ -184,9 +184,7 @@ __device__ float2* warp_dft(float2* a, float2* b, const float2* T, const GenPlan
                 float2 A0 = b[j0], B0 = make_float2(0.f, 0.f);
                 float2 A1 = b[j1], B1 = make_float2(0.f, 0.f);
                 int m0 = 0, m1 = 0;
-                // unrolled: the next terms' shared-memory loads overlap this term's FMAs (the
-                // accumulation order is unchanged)
-#pragma unroll 3
+#pragma unroll 1
                 for (int q = 1; q <= h; ++q) {
                     m0 += qp0;
                     if (m0 >= r) m0 -= r;
