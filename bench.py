@@ -228,6 +228,78 @@ def np_ones8():
 PAPER_SPEEDUP = "4~15x whole-volume CPU -> GPU (Sec. III; the paper names no CPU or GPU model)"
 
 
+def cufft_comparison(field, mask, lam, tau, sigma, n_iter, stream, chi_fused):
+    """Comparison points on the same volume, in plain PyTorch on the GPU (cuFFT for the transforms):
+    (1) the FFT passes alone -- per iteration two forward and two inverse real 2-D FFTs of the
+    volume; (2) the whole iteration unfused, one library call per step (the structure of the
+    paper's GPU method: transforms by a library, every pointwise step its own kernel).  Not the
+    product path; (2)'s chi is checked against the fused kernel's."""
+    import torch
+
+    S, H, W = field.shape
+    dev = field.device
+    ky = torch.fft.fftfreq(H, device=dev, dtype=torch.float64)[:, None]
+    kx = torch.fft.rfftfreq(W, device=dev, dtype=torch.float64)[None, :]
+    k2 = kx * kx + ky * ky
+    D = torch.where(k2 > 0, 1.0 / 3.0 - ky * ky / torch.where(k2 > 0, k2, 1.0), torch.zeros_like(k2)).float()
+    x = torch.zeros_like(field)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(2):  # warm the plans
+            x = torch.fft.irfft2(D * torch.fft.rfft2(x), s=(H, W))
+        e0.record(stream)
+        for _ in range(n_iter):
+            x = torch.fft.irfft2(D * torch.fft.rfft2(x), s=(H, W))
+            x = torch.fft.irfft2(D * torch.fft.rfft2(x), s=(H, W))
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fft = e0.elapsed_time(e1)
+
+    def Dop(a):
+        return torch.fft.irfft2(D * torch.fft.rfft2(a), s=(H, W))
+
+    w = mask.float()
+    b = w * field
+    chi = torch.zeros_like(field)
+    cb = torch.zeros_like(field)
+    p = torch.zeros_like(field)
+    qx = torch.zeros_like(field)
+    qy = torch.zeros_like(field)
+    inv = 1.0 / (1.0 + sigma / lam)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(n_iter):
+            p = (p + sigma * (w * Dop(cb) - b)) * inv
+            gx = torch.zeros_like(cb)
+            gy = torch.zeros_like(cb)
+            gx[:, :, :-1] = cb[:, :, 1:] - cb[:, :, :-1]
+            gy[:, :-1, :] = cb[:, 1:, :] - cb[:, :-1, :]
+            qx = torch.clamp(qx + sigma * w * gx, -1.0, 1.0)
+            qy = torch.clamp(qy + sigma * w * gy, -1.0, 1.0)
+            d = torch.zeros_like(cb)
+            d[:, :, 1:] += qx[:, :, :-1]
+            d[:, :, :-1] -= qx[:, :, :-1]
+            d[:, 1:, :] += qy[:, :-1, :]
+            d[:, :-1, :] -= qy[:, :-1, :]
+            new = chi - tau * Dop(w * p) - tau * d
+            cb = 2.0 * new - chi
+            chi = new
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_unfused = e0.elapsed_time(e1)
+    rel = float(torch.linalg.norm((chi - chi_fused).double()) / torch.linalg.norm(chi_fused.double()))
+    work = S * H * W * n_iter
+    return {
+        "cufft_fft_passes_only": {"ms": ms_fft, "voxel_iter_per_s": work / (ms_fft * 1e-3),
+                                  "note": "2 rfft2 + 2 irfft2 of the volume per iteration (torch.fft = cuFFT)"},
+        "unfused_library_loop": {"ms": ms_unfused, "voxel_iter_per_s": work / (ms_unfused * 1e-3),
+                                 "rel_l2_vs_fused_chi": rel,
+                                 "note": "the same iteration as cuFFT transforms plus one elementwise kernel per "
+                                         "step, launched from the host (plain PyTorch)"},
+    }
+
+
 def run_reference(args):
     """The oracle (this method's reference implementation) timed on every host core: each step
     solves one slice per core of the workload, 100 iterations each, in a spawn process pool."""
@@ -382,6 +454,10 @@ def run_native(args):
                  "launches": SLICES, "note": "64 sequential single-slice solves, same kernel"}
         pcs.pcs_destroy(ctx1)
     pcs.pcs_destroy(ctx)
+    cufft = None
+    if args.cufft and rank == 0:
+        cufft = cufft_comparison(field, mask, LAM, tau, sigma, N_ITER, stream, chi)
+        assert cufft["unfused_library_loop"]["rel_l2_vs_fused_chi"] <= 1e-4, cufft
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()
@@ -433,6 +509,10 @@ def run_native(args):
             "wall_s_timed_region": t_wall,
             "L": L,
         }
+        if cufft is not None:
+            cufft["fused_vs_unfused"] = cufft["unfused_library_loop"]["ms"] / ms_step
+            cufft["fused_vs_fft_passes_only"] = cufft["cufft_fft_passes_only"]["ms"] / ms_step
+            line["vs_cufft"] = cufft
         if pool is not None:
             cv, dt = cpu_oracle_sample(pb, tau, sigma, 4, N_ITER)
             n_all = pool._processes
@@ -1047,6 +1127,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
+    ap.add_argument("--cufft", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time cuFFT doing the FFT passes alone and the unfused library loop (comparison)")
     ap.add_argument("--plain-loop", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the plain per-slice GPU loop (one timed volume)")
     ap.add_argument("--workload", choices=["volume", "serve", "volume3d", "fieldmap", "native", "uneven"],

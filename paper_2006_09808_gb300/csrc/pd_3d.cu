@@ -60,6 +60,9 @@ const Slice3Entry k_slice3[] = {
     slice3_entry<Geo<64, 64, 1>>(),
     slice3_entry<Geo<128, 128, 2>>(),
     slice3_entry<Geo<256, 256, 4, 2>>(),
+    // one 512-thread CTA per SM: 36 clusters, two slices per cluster for 64 slices (the last entry
+    // of a size is the one used)
+    slice3_entry<Geo<256, 256, 4, 1, 512>>(),
 };
 
 struct Z3Entry {

@@ -137,6 +137,9 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd3_slice_kernel(P3Params a) {
         }
         cluster_barrier<G::C>();  // all scatters in; all gathers done
         if (a.store) columns_out_3d<G>(cx, a.spec, s);
+        // a cluster with several slices: the next slice's zero start writes these columns with
+        // another thread mapping than the store just read them with
+        __syncthreads();
     }
 }
 

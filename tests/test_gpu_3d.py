@@ -50,7 +50,8 @@ def gpu3(field, mask, lam, n_iter, tv=0, weight=None, voxel=None):
 
 @pytest.mark.parametrize(
     "S,H,n_iter,lam,tv",
-    [(32, 64, 100, 1.0, 0), (32, 64, 100, 1.0, 1), (64, 64, 60, 1e-3, 0), (32, 128, 50, 1.0, 0)],
+    [(32, 64, 100, 1.0, 0), (32, 64, 100, 1.0, 1), (64, 64, 60, 1e-3, 0), (32, 128, 50, 1.0, 0),
+     (128, 128, 10, 1.0, 0)],  # 128 slices: the z transform of length 128, several slices per cluster
 )
 def test_parity_3d(S, H, n_iter, lam, tv):
     pb = phantoms.volume(H, H, S, seed=51, lam=lam, n_iter=n_iter)
@@ -98,6 +99,18 @@ def test_parity_3d_full_size_volume():
     assert rel_l2(got, ref) <= TOL
     m = pb.mask.astype(bool)
     assert rel_l2(got[m], ref[m]) <= TOL
+
+
+def test_parity_3d_more_slices_than_resident_clusters():
+    """256 x 256 x 128: more slices than the slice kernel's resident clusters, so clusters take
+    several slices per launch; against the whole-volume oracle."""
+    pb = phantoms.volume(256, 256, 128, seed=55, lam=5e-4, n_iter=6)
+    ref = O3.pd_solve_3d(pb.field.astype(np.float64), pb.mask, pb.lam, STEP, STEP, pb.n_iter)
+    got = gpu3(pb.field, pb.mask, pb.lam, pb.n_iter)
+    assert np.all(np.isfinite(got))
+    assert rel_l2(got, ref) <= TOL
+    for s in (0, 63, 64, 127):
+        assert rel_l2(got[s], ref[s]) <= 10 * TOL, s
 
 
 def test_3d_edge_cases_and_errors():
