@@ -71,3 +71,25 @@ def test_early_stop_per_slice():
             assert r["gap"] <= tol * r["objective"]
         ref = _plain(pb, r["iters"], tau, kernel=pcs.KERNEL_STREAMING)
         assert np.array_equal(got[s], ref[s]), s
+
+
+def test_monitored_with_more_slices_than_resident_clusters():
+    """40 slices of 256 x 256 (the default variant keeps 36 clusters resident, so clusters take
+    several slices per chunk on the plain persistent loop, and the report kernel several slices
+    per launch): chunked == one straight solve bit for bit, and two sampled slices' FP64 reports
+    against the oracle's diagnostics."""
+    from oracle import pd_oracle as O
+
+    pb = phantoms.volume(256, 256, 40, seed=44, lam=10.0, n_iter=120)
+    tau = 1.0 / 2.8333
+    got, rep = _monitored(pb, 120, tau, 50, 0.0)
+    ref = _plain(pb, 120, tau, kernel=pcs.KERNEL_STREAMING)
+    assert np.array_equal(got, ref)
+    assert all(r["iters"] == 120 for r in rep)
+    for s in (0, 39):
+        st = O.pd_solve(pb.field[s].astype(np.float64), pb.mask[s], pb.lam, tau, tau, 120, return_state=True)
+        d = O.diagnostics(st, pb.field[s].astype(np.float64), pb.mask[s], pb.lam)
+        assert np.linalg.norm(got[s] - st.chi) / np.linalg.norm(st.chi) <= 1e-4, s
+        assert rep[s]["objective"] == pytest.approx(d.primal, rel=1e-4), s
+        assert rep[s]["data_residual"] == pytest.approx(d.data_residual, rel=1e-4), s
+        assert rep[s]["gap"] == pytest.approx(d.gap, rel=2e-2, abs=1e-4 * d.primal), s
