@@ -153,6 +153,25 @@ def test_resident_and_streaming_kernels_agree_at_full_size():
         assert rel_l2(a[s], b[s]) <= 1e-5, s
 
 
+@pytest.mark.parametrize("H,S,cluster_size", [(128, 48, 4), (64, 200, 1)])
+def test_resident_kernel_with_more_slices_than_resident_clusters(H, S, cluster_size):
+    """The resident kernel's slice loop, with more slices than clusters on the GPU at
+    once: every cluster solves several slices in turn, each from a zero start.  Each
+    sampled slice must equal, bit for bit, the same slice solved alone, and the oracle
+    within the tolerance."""
+    pb = phantoms.volume(H, H, S, seed=37, lam=5e-4, n_iter=60)
+    L, tau, sigma = steps(H, H)
+    opts = dict(kernel=RESIDENT, cluster_size=cluster_size)
+    got = gpu_solve(pb.field, pb.mask, pb.lam, tau, sigma, pb.n_iter, **opts)
+    assert np.all(np.isfinite(got))
+    for s in (0, S // 2, S - 1):
+        alone = gpu_solve(pb.field[s:s + 1], pb.mask[s:s + 1], pb.lam, tau, sigma, pb.n_iter, **opts)
+        assert np.array_equal(got[s], alone[0]), s
+    for s in (0, S - 1):
+        ref = oracle_solve(pb.field[s], pb.mask[s], pb.lam, tau, sigma, pb.n_iter)
+        assert rel_l2(got[s], ref) <= TOL, s
+
+
 def test_config2_full_size_sampled_slices():
     """256 x 256 x 64, 500 iterations, in the bench's launch configuration; the
     oracle solves three sampled slices (first, middle, last)."""
