@@ -29,7 +29,7 @@ struct Slice3Entry {
     int H, W, C;
     size_t smem;
     cudaError_t (*prepare)(int* max_clusters);
-    cudaError_t (*launch)(const P3Params& a, int n_clusters, cudaStream_t st);
+    cudaError_t (*launch)(const P3Params& a, int n_clusters, cudaStream_t st, bool pdl);
     cudaError_t (*prepare_report)(int* max_clusters);
     cudaError_t (*launch_report)(const P3Report& r, int n_clusters, cudaStream_t st);
 };
@@ -38,9 +38,25 @@ template <class G>
 cudaError_t prepare3(int* mc) {
     return pcs::prepare_cluster<G>(pcs::pd3_slice_kernel<G>, G::SMEM_BYTES, mc);
 }
+// pdl: programmatic dependent launch (the kernel waits for the previous grid before it
+// touches memory, so its prologue overlaps that grid's tail)
 template <class G>
-cudaError_t launch3(const P3Params& a, int ncl, cudaStream_t st) {
-    return pcs::launch_cluster<G>(pcs::pd3_slice_kernel<G>, a, G::SMEM_BYTES, ncl, st);
+cudaError_t launch3(const P3Params& a, int ncl, cudaStream_t st, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ncl * G::C, 1, 1);
+    cfg.blockDim = dim3(G::NT, 1, 1);
+    cfg.dynamicSmemBytes = G::SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, pcs::pd3_slice_kernel<G>, a);
 }
 template <class G>
 cudaError_t prepare3_report(int* mc) {
@@ -67,15 +83,25 @@ const Slice3Entry k_slice3[] = {
 
 struct Z3Entry {
     int NZ, H, W;
-    cudaError_t (*launch)(float2* spec, const float2* twid, int ntw, float3 iv, cudaStream_t st);
+    cudaError_t (*launch)(float2* spec, const float2* twid, int ntw, float3 iv, cudaStream_t st, bool pdl);
 };
 
+// z pass: one CTA per tile of pencils
 template <int NZ, int H, int W>
-cudaError_t launch_z(float2* spec, const float2* twid, int ntw, float3 iv, cudaStream_t st) {
+cudaError_t launch_z(float2* spec, const float2* twid, int ntw, float3 iv, cudaStream_t st, bool pdl) {
     using GZ = GeoZ<NZ, H, W>;
-    const dim3 grid(GZ::M + 1, H / GZ::TY);
-    pcs::pd3_z_kernel<GZ, NZ, H, W><<<grid, 256, GZ::SMEM_BYTES, st>>>(spec, twid, ntw, iv);
-    return cudaGetLastError();
+    auto kern = pcs::pd3_z_kernel<GZ, NZ, H, W>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(GZ::NTILES, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = GZ::SMEM_BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, spec, static_cast<const float2*>(twid), ntw, iv);
 }
 
 const Z3Entry k_z3[] = {
@@ -185,18 +211,23 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
         // iteration n: dual step from the spectrum of chibar_n (zero at n = 0), z pass,
         // primal step, z pass (the spectrum of chibar_{n+1}; not after the last)
         for (int it = 0; it < n_iter && ret == PCS_OK; ++it) {
+            // serpentine slice order: each launch starts on the slices the one before ended on,
+            // whose state is the most likely to be still in L2
             a.phase = 0;
             a.load = it > 0;
             a.store = 1;
-            if ((e = se->launch(a, ncl, st)) != cudaSuccess || (e = ze->launch(spec, twid, ntw, iv, st)) != cudaSuccess) {
+            a.reverse = 0;
+            if ((e = se->launch(a, ncl, st, it > 0)) != cudaSuccess ||
+                (e = ze->launch(spec, twid, ntw, iv, st, true)) != cudaSuccess) {
                 ret = fail3(PCS_ECUDA, "launch", e);
                 break;
             }
             a.phase = 1;
             a.load = 1;
             a.store = it + 1 < n_iter;
-            if ((e = se->launch(a, ncl, st)) != cudaSuccess ||
-                (a.store && (e = ze->launch(spec, twid, ntw, iv, st)) != cudaSuccess)) {
+            a.reverse = 1;
+            if ((e = se->launch(a, ncl, st, true)) != cudaSuccess ||
+                (a.store && (e = ze->launch(spec, twid, ntw, iv, st, true)) != cudaSuccess)) {
                 ret = fail3(PCS_ECUDA, "launch", e);
                 break;
             }
@@ -218,7 +249,7 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
                 for (int mode = 0; mode < 3 && ret == PCS_OK; ++mode) {
                     r.mode = mode;
                     if ((e = se->launch_report(r, ncl_rep, st)) != cudaSuccess ||
-                        (mode < 2 && (e = ze->launch(spec, twid, ntw, iv, st)) != cudaSuccess))
+                        (mode < 2 && (e = ze->launch(spec, twid, ntw, iv, st, false)) != cudaSuccess))
                         ret = fail3(PCS_ECUDA, "report launch", e);
                 }
             }

@@ -103,12 +103,20 @@ __device__ __forceinline__ void columns_out_3d(const Ctx<G>& cx, float2* __restr
     }
 }
 
+// Wait for the grid this launch depends on (programmatic dependent launch): a no-op for a
+// launch without that attribute.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the next launch in the stream start its prologue (it still waits for this grid's end
+// before it touches memory this grid writes).
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 struct P3Params {
     PDParams pd;     // state, tables, steps (pd.S = slices of the volume; pd.qz set)
     float2* spec;    // [S][M+1][H]
     int phase;       // 0: dual step, 1: primal step
     int load;        // 1: start from the stored spectrum; 0: zero spectrum (chibar = 0)
     int store;       // 1: store the spectrum of the phase's output
+    int reverse;     // 1: clusters take the slices from the last one down
 };
 
 template <class G>
@@ -121,8 +129,11 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd3_slice_kernel(P3Params a) {
     const int ncl = gridDim.x / G::C;
     constexpr size_t SLICE = (size_t)G::H * G::W;
     __syncthreads();  // twiddle tables
+    grid_dependents_launch();
+    grid_dependency_wait();  // the previous launch's spectrum and state complete
 #pragma unroll 1
-    for (int s = cid; s < prm.S; s += ncl) {
+    for (int k = cid; k < prm.S; k += ncl) {
+        const int s = a.reverse ? prm.S - 1 - k : k;
         const size_t base = (size_t)s * SLICE;
         if (a.load) {
             columns_in_3d<G>(cx, a.spec, s);
@@ -278,59 +289,71 @@ __global__ void __launch_bounds__(G::NT, 1) pd3_report_kernel(P3Report r) {
     }
 }
 
-// z pass: pencils of TZ = NZ / EZ lanes, one per (kx, ky); a CTA takes
-// NW * 32 / TZ consecutive ky of one kx.  D(k) = 1/3 - kz^2 / |k|^2 (D(0) = 0)
-// in FP32, k_i = f_i * iv_i: the integer frequencies in cycles per sample times the
-// inverse voxel edges (iv = (1, 1, 1) for isotropic voxels).
+// z pass: pencils of TZ = NZ / EZ lanes, one per (kx, ky); a tile is NW * 32 / TZ
+// consecutive ky of one kx, so that every load is a full 32-byte sector.  D(k) = 1/3 -
+// kz^2 / |k|^2 (D(0) = 0) in FP32, k_i = f_i * iv_i: the integer frequencies in cycles per
+// sample times the inverse voxel edges (iv = (1, 1, 1) for isotropic voxels).  One tile per
+// CTA (grid NTILES): a persistent form that kept the next tile's loads in flight took 74
+// registers instead of 57, three CTAs per SM instead of four, and measured slower.
 template <int NZ, int H, int W, int NT = 256>
 struct GeoZ {
     static constexpr int EZ = default_elems(NZ);
     static constexpr int TZ = NZ / EZ;
     static constexpr int PPW = 32 / TZ;           // pencils per warp
-    static constexpr int TY = (NT / 32) * PPW;    // pencils (ky values) per CTA
+    static constexpr int TY = (NT / 32) * PPW;    // pencils (ky values) per tile
     static constexpr int M = W / 2;
+    static constexpr int NTILES = (M + 1) * (H / TY);
     static constexpr int NP = NZ + (TZ % 16);  // pencil buffer stride: adjacent pencils on other banks
     static constexpr size_t SMEM_BYTES = sizeof(float2) * (TY * NP + StageTw<NZ, EZ>::SIZE);
     static_assert(H % TY == 0, "ky tiles");
+    static_assert((NZ & (NZ - 1)) == 0 && (H & (H - 1)) == 0 && (W & (W - 1)) == 0,
+                  "powers of two: i / n == i * (1 / n) exactly");
 };
 
-__device__ __forceinline__ float signed_freq(int k, int n) { return (float)(k < (n + 1) / 2 ? k : k - n) / (float)n; }
+// Signed frequency of index k of a length-n transform in cycles per sample (n a power of two,
+// so the product with the reciprocal equals the quotient).
+template <int N>
+__device__ __forceinline__ float signed_freq_pow2(int k) {
+    return (float)(k < (N + 1) / 2 ? k : k - N) * (1.0f / (float)N);
+}
 
 template <class GZ, int NZ, int H, int W>
 __global__ void __launch_bounds__(256) pd3_z_kernel(float2* __restrict__ spec, const float2* __restrict__ twid,
                                                     int ntw, float3 iv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int TZ = GZ::TZ, EZ = GZ::EZ, M = GZ::M;
+    constexpr int TZ = GZ::TZ, EZ = GZ::EZ, M = GZ::M, TILES_Y = H / GZ::TY;
+    constexpr size_t STRIDE = (size_t)(M + 1) * H;  // between slices
     float2* buf = reinterpret_cast<float2*>(smem_raw);
     float2* stw = buf + GZ::TY * GZ::NP;
     StageTw<NZ, EZ>::fill(stw, twid, ntw / NZ, threadIdx.x, 256);
     __syncthreads();
+    grid_dependents_launch();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % TZ;
     const int pen = warp * GZ::PPW + lane / TZ;
     const unsigned gm = group_mask<TZ>(lane);
-    const int kx = blockIdx.x;
-    const int ky = blockIdx.y * GZ::TY + pen;
-    const size_t stride = (size_t)(M + 1) * H;
-    float2* col = spec + (size_t)kx * H + ky;
     float2* pb = buf + pen * GZ::NP;
+    constexpr float scale = 1.0f / ((float)NZ * (float)H * (float)W);
+    grid_dependency_wait();
+    const int t = blockIdx.x;
+    const int kx = t / TILES_Y, ky = (t - kx * TILES_Y) * GZ::TY + pen;
+    float2* col = spec + (size_t)kx * H + ky;
     float2 x[EZ];
 #pragma unroll
-    for (int e = 0; e < EZ; ++e) x[e] = __ldcg(col + (size_t)(g + TZ * e) * stride);
+    for (int e = 0; e < EZ; ++e) x[e] = __ldcg(col + (size_t)(g + TZ * e) * STRIDE);
     fft<NZ, TZ, false>(x, pb, stw, g, gm);
-    const float fx = (float)kx / (float)W * iv.x, fy = signed_freq(ky, H) * iv.y;
+    const float fx = (float)kx * (1.0f / (float)W) * iv.x, fy = signed_freq_pow2<H>(ky) * iv.y;
     const float pxy = fx * fx + fy * fy;
-    const float scale = 1.0f / ((float)NZ * (float)H * (float)W);
 #pragma unroll
     for (int e = 0; e < EZ; ++e) {
-        const float fz = signed_freq(g + TZ * e, NZ) * iv.z;
+        const float fz = signed_freq_pow2<NZ>(g + TZ * e) * iv.z;
         const float k2 = pxy + fz * fz;
         const float d = (k2 > 0.f) ? (1.0f / 3.0f - (fz * fz) / k2) * scale : 0.f;
         x[e] = make_float2(x[e].x * d, x[e].y * d);
     }
     fft<NZ, TZ, true>(x, pb, stw, g, gm);
 #pragma unroll
-    for (int e = 0; e < EZ; ++e) __stcg(col + (size_t)(g + TZ * e) * stride, x[e]);
+    for (int e = 0; e < EZ; ++e) __stcg(col + (size_t)(g + TZ * e) * STRIDE, x[e]);
 }
 
 }  // namespace pcs

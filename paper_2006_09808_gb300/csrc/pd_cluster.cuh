@@ -422,6 +422,10 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
 // move ahead of this chunk's stores).  2 measured fastest (4: +3%, 8: +13%).
 constexpr int kChunk = 2;
 
+// Elements of one slice (the 3-D variant's offset between neighbouring slices).
+template <class G>
+constexpr size_t SL3 = (size_t)G::H * G::W;
+
 // Phase B: u = D chibar -> dual proxes -> forward transform of W p.
 // q stays exactly zero wherever the 0/1 mask M is zero (zero start, masked
 // increments), so M q = q; p likewise wherever W is zero.  With W = mask the
@@ -451,6 +455,7 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
     Real* __restrict__ pp = prm.p;
     Real* __restrict__ qxp = prm.qx;
     Real* __restrict__ qyp = prm.qy;
+    Real* __restrict__ qzp = prm.qz;  // 3-D variant only
 #pragma unroll 1
     for (int pass = 0; pass < G::R / G::RPP; ++pass) {
         const int i = cx.crank * G::R + pass * G::RPP + grp;
@@ -470,6 +475,7 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
 #pragma unroll
         for (int e0 = 0; e0 < ER; e0 += CH) {
             V f[CH], p[CH], cd[CH], qx[CH], qy[CH];
+            V qz[CH], cz[CH];  // 3-D variant only
             uchar2 mk[CH];
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
@@ -480,6 +486,10 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
                 cd[c] = has_down ? __ldcg(reinterpret_cast<const V*>(cbar + o + W)) : cb[e0 + c];
                 qx[c] = __ldcg(reinterpret_cast<const V*>(qxp + o));
                 qy[c] = __ldcg(reinterpret_cast<const V*>(qyp + o));
+                if constexpr (Z3) {  // with the chunk's other loads, ahead of its stores
+                    qz[c] = __ldcg(reinterpret_cast<const V*>(qzp + o));
+                    cz[c] = (s + 1 < prm.S) ? __ldcg(reinterpret_cast<const V*>(cbar + o + SL3<G>)) : cb[e0 + c];
+                }
             }
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
@@ -508,16 +518,14 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
                 qyn.x = qy[c].x + sigma * m0 * (cd[c].x - cb[e].x);
                 qyn.y = qy[c].y + sigma * m1 * (cd[c].y - cb[e].y);
                 if constexpr (Z3) {
-                    constexpr size_t SL = (size_t)G::H * G::W;
-                    V qzn = __ldcg(reinterpret_cast<const V*>(prm.qz + o));
+                    V qzn = qz[c];
                     if (s + 1 < prm.S) {
-                        const V cz = __ldcg(reinterpret_cast<const V*>(cbar + o + SL));
-                        qzn.x += sigma * m0 * (cz.x - cb[e].x);
-                        qzn.y += sigma * m1 * (cz.y - cb[e].y);
+                        qzn.x += sigma * m0 * (cz[c].x - cb[e].x);
+                        qzn.y += sigma * m1 * (cz[c].y - cb[e].y);
                     }
                     tv_prox3(qxn.x, qyn.x, qzn.x, prm.tv_iso);
                     tv_prox3(qxn.y, qyn.y, qzn.y, prm.tv_iso);
-                    __stcg(reinterpret_cast<V*>(prm.qz + o), qzn);
+                    __stcg(reinterpret_cast<V*>(qzp + o), qzn);
                 } else {
                     tv_prox(qxn.x, qyn.x, prm.tv_iso);
                     tv_prox(qxn.y, qyn.y, prm.tv_iso);
@@ -555,6 +563,7 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
     const Real tau = prm.tau;
     const Real* __restrict__ qxp = prm.qx;
     const Real* __restrict__ qyp = prm.qy;
+    const Real* __restrict__ qzp = prm.qz;  // 3-D variant only
     Real* __restrict__ chip = prm.chi;
     Real* __restrict__ cbar = prm.chibar;
 #pragma unroll 1
@@ -574,12 +583,17 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
 #pragma unroll
         for (int e0 = 0; e0 < ER; e0 += CH) {
             V qy[CH], qu[CH], chi[CH];
+            V zc[CH], zp[CH];  // 3-D variant only: qz of this slice and of the slice before
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const size_t o = rowoff + 2 * (g + TR * (e0 + c));
                 qy[c] = __ldcg(reinterpret_cast<const V*>(qyp + o));
                 qu[c] = has_up ? __ldcg(reinterpret_cast<const V*>(qyp + o - W)) : mk<V>(Real(0), Real(0));
                 chi[c] = __ldcg(reinterpret_cast<const V*>(chip + o));
+                if constexpr (Z3) {  // with the chunk's other loads, ahead of its stores
+                    zc[c] = (s + 1 < prm.S) ? __ldcg(reinterpret_cast<const V*>(qzp + o)) : mk<V>(Real(0), Real(0));
+                    zp[c] = (s > 0) ? __ldcg(reinterpret_cast<const V*>(qzp + o - SL3<G>)) : mk<V>(Real(0), Real(0));
+                }
             }
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
@@ -596,12 +610,8 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
                 Real d0 = (al - qx[e].x) + (qu[c].x - b0);
                 Real d1 = (qx[e].x - a1r) + (qu[c].y - b1);
                 if constexpr (Z3) {
-                    constexpr size_t SL = (size_t)G::H * G::W;
-                    V zc = mk<V>(Real(0), Real(0)), zp = mk<V>(Real(0), Real(0));
-                    if (s + 1 < prm.S) zc = __ldcg(reinterpret_cast<const V*>(prm.qz + o));
-                    if (s > 0) zp = __ldcg(reinterpret_cast<const V*>(prm.qz + o - SL));
-                    d0 += zp.x - zc.x;
-                    d1 += zp.y - zc.y;
+                    d0 += zp[c].x - zc[c].x;
+                    d1 += zp[c].y - zc[c].y;
                 }
                 V cn;
                 cn.x = chi[c].x - tau * v.x - tau * d0;
