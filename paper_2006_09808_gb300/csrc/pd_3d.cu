@@ -39,7 +39,7 @@ cudaError_t prepare3(int* mc) {
     return pcs::prepare_cluster<G>(pcs::pd3_slice_kernel<G>, G::SMEM_BYTES, mc);
 }
 // pdl: programmatic dependent launch (the kernel waits for the previous grid before it
-// touches memory, so its prologue overlaps that grid's tail)
+// touches memory; its launch overlaps the end of that grid)
 template <class G>
 cudaError_t launch3(const P3Params& a, int ncl, cudaStream_t st, bool pdl) {
     cudaLaunchConfig_t cfg = {};

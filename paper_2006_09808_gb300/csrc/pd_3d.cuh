@@ -103,13 +103,6 @@ __device__ __forceinline__ void columns_out_3d(const Ctx<G>& cx, float2* __restr
     }
 }
 
-// Wait for the grid this launch depends on (programmatic dependent launch): a no-op for a
-// launch without that attribute.
-__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-// Let the next launch in the stream start its prologue (it still waits for this grid's end
-// before it touches memory this grid writes).
-__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
-
 struct P3Params {
     PDParams pd;     // state, tables, steps (pd.S = slices of the volume; pd.qz set)
     float2* spec;    // [S][M+1][H]
@@ -129,7 +122,6 @@ __global__ void __launch_bounds__(G::NT, G::MINB) pd3_slice_kernel(P3Params a) {
     const int ncl = gridDim.x / G::C;
     constexpr size_t SLICE = (size_t)G::H * G::W;
     __syncthreads();  // twiddle tables
-    grid_dependents_launch();
     grid_dependency_wait();  // the previous launch's spectrum and state complete
 #pragma unroll 1
     for (int k = cid; k < prm.S; k += ncl) {
@@ -327,7 +319,6 @@ __global__ void __launch_bounds__(256) pd3_z_kernel(float2* __restrict__ spec, c
     float2* stw = buf + GZ::TY * GZ::NP;
     StageTw<NZ, EZ>::fill(stw, twid, ntw / NZ, threadIdx.x, 256);
     __syncthreads();
-    grid_dependents_launch();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % TZ;
     const int pen = warp * GZ::PPW + lane / TZ;

@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(kGenRowWarps * 32) gen_rows_kernel(GenParams g
     float2* T = reinterpret_cast<float2*>(smem_raw);
     for (int t = threadIdx.x; t < W; t += blockDim.x) T[t] = g.trow[t];
     __syncthreads();
+    grid_dependency_wait();  // the previous launch's spectrum and state complete
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int pair = blockIdx.x * kGenRowWarps + warp;
     if (pair >= g.S * (H / 2)) return;  // whole warps; no CTA barrier below
@@ -666,6 +667,7 @@ __global__ void __launch_bounds__(kGenColTile * 32) gen_cols_kernel(GenParams g)
     const int ncol = min(kGenColTile, M1 - kx0);
     float2* spec = g.spec + (size_t)s * H * M1;
     for (int t = threadIdx.x; t < H; t += blockDim.x) T[t] = g.tcol[t];
+    grid_dependency_wait();  // the previous launch's spectrum complete
     // rows of the tile: adjacent threads take adjacent columns
     const int c = threadIdx.x % kGenColTile;
     const int ky0 = threadIdx.x / kGenColTile;
@@ -727,6 +729,7 @@ __global__ void __launch_bounds__(GeoCol<H>::NT) gen_cols_fft_kernel(GenParams g
     float2* stw = buf + GC::TY * GC::NP;
     StageTw<H, EZ>::fill(stw, g.tcol, 1, threadIdx.x, GC::NT);
     __syncthreads();
+    grid_dependency_wait();  // the previous launch's spectrum complete
     const int W = g.W, M1 = g.M1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gi = lane % TZ;
