@@ -198,6 +198,37 @@ def test_any_size_context():
     assert ei.value.status == pcs.PCS_EUNSUPPORTED
 
 
+def test_any_size_solve_captured_in_a_cuda_graph():
+    """The any-size iteration loop (every launch after the first a programmatic dependent
+    launch) captured by the caller in a CUDA graph: each replay equals the direct solve bit for
+    bit, and the oracle within the tolerance."""
+    pb = phantoms.volume(128, 132, 3, seed=81, lam=5e-4, n_iter=30)
+    f = torch.from_numpy(np.array(pb.field, dtype=np.float32)).cuda()
+    m = torch.from_numpy(np.array(pb.mask, dtype=np.uint8)).cuda()
+    stream = torch.cuda.Stream()
+    ctx = pcs.pcs_create(128, 132, 3, stream=stream)
+    try:
+        torch.cuda.synchronize()
+        direct = torch.empty_like(f)
+        with torch.cuda.stream(stream):
+            pcs.pcs_solve_slices(ctx, f, m, pb.lam, STEP, STEP, pb.n_iter, direct)
+        stream.synchronize()
+        captured = torch.full_like(f, float("nan"))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            pcs.pcs_solve_slices(ctx, f, m, pb.lam, STEP, STEP, pb.n_iter, captured)
+        for _ in range(2):
+            captured.fill_(float("nan"))
+            torch.cuda.synchronize()
+            graph.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(captured, direct)
+        pcs.pcs_check(ctx)
+    finally:
+        pcs.pcs_destroy(ctx)
+    assert rel_l2(direct.cpu().numpy(), oracle(pb.field, pb.mask, pb.lam, pb.n_iter)) <= TOL
+
+
 @pytest.mark.parametrize("H,W,tv,weighted,b0", [(128, 132, 0, False, 0), (256, 258, 1, False, 0),
                                                 (90, 98, 0, True, 1)])
 def test_generic_report_against_oracle(H, W, tv, weighted, b0):
