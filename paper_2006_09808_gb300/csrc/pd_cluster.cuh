@@ -293,11 +293,18 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const typename G::
         V x[EC];
 #pragma unroll
         for (int e = 0; e < EC; ++e) x[e] = col[P(g + TC * e, key)];
+        // the column's D(k) entries (Dm, Dd for the packed column), in flight during the FFT
+        Real dk[EC], ddk[EC];
+        const Real* d = dtab + (size_t)kx * H;
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            dk[e] = __ldg(d + g + TC * e);
+            ddk[e] = (kx == 0) ? __ldg(ddtab + g + TC * e) : Real(0);
+        }
         fft<H, TC, false>(x, col, cx.stw_c, g, gm, key);
         if (kx != 0) {
-            const Real* d = dtab + (size_t)kx * H;
 #pragma unroll
-            for (int e = 0; e < EC; ++e) x[e] = cscale(x[e], __ldg(d + g + TC * e));
+            for (int e = 0; e < EC; ++e) x[e] = cscale(x[e], dk[e]);
         } else {
             // packed DC / Nyquist column: pair ky with -ky
 #pragma unroll
@@ -307,7 +314,7 @@ __device__ __forceinline__ void column_pass(const Ctx<G>& cx, const typename G::
             for (int e = 0; e < EC; ++e) {
                 const int ky = g + TC * e;
                 const V ym = col[P((H - ky) % H, key)];
-                const Real dm = __ldg(dtab + ky), dd = __ldg(ddtab + ky);
+                const Real dm = dk[e], dd = ddk[e];
                 x[e] = mk<V>(fma(dm, x[e].x, dd * ym.x), fma(dm, x[e].y, -dd * ym.y));
             }
         }
