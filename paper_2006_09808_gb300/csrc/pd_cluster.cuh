@@ -434,7 +434,7 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
 
 // Epilogue element chunk: the loads of CH elements are issued together, then
 // computed and stored (restrict-qualified pointers let the next chunk's loads
-// move ahead of this chunk's stores).  2 measured fastest (4: +3%, 8: +13%).
+// move ahead of this chunk's stores).  2 measured fastest (1: +1.7%, 4: +3%, 8: +13%).
 constexpr int kChunk = 2;
 
 // Elements of one slice (the 3-D variant's offset between neighbouring slices).
