@@ -111,6 +111,71 @@ const Z3Entry k_z3[] = {
     {64, 256, 256, &launch_z<64, 256, 256>},  {128, 256, 256, &launch_z<128, 256, 256>},
 };
 
+// Pencil form (pd_3d.cuh): row kernel geometry per slice size (one row pass per CTA, two
+// 256-thread CTAs per SM) and plane kernel per (S, H) (1024 threads where the plane, its z
+// scratch and tables fit in shared memory, else 512).
+template <int H>
+using GeoRows3 = Geo<H, H, H / ((256 / 32) * (32 / (H / 2 / pcs::default_elems(H / 2)))), 2, 256>;
+
+struct Pencil3Entry {
+    int S, H, W;
+    cudaError_t (*prepare)();
+    cudaError_t (*launch_rows)(const P3Params& a, cudaStream_t st, bool pdl);
+    cudaError_t (*launch_planes)(float2* spec, const float2* twid, int ntw, float3 iv, cudaStream_t st, bool pdl);
+};
+
+cudaError_t launch_dep3(const void* kern, void** args, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                        bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, kern, args);
+}
+
+template <int S, int H, int NT>
+cudaError_t prepare_pencil() {
+    using GR = GeoRows3<H>;
+    using GP = pcs::GeoPlane<S, H, H, NT>;
+    cudaError_t e = cudaFuncSetAttribute(pcs::pd3p_rows_kernel<GR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pcs::pencil_rows_smem<GR>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pcs::pd3p_plane_kernel<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)GP::SMEM_BYTES);
+}
+template <int S, int H, int NT>
+cudaError_t launch_pencil_rows(const P3Params& a, cudaStream_t st, bool pdl) {
+    using GR = GeoRows3<H>;
+    P3Params arg = a;
+    void* args[] = {&arg};
+    return launch_dep3(reinterpret_cast<const void*>(pcs::pd3p_rows_kernel<GR>), args, dim3(S * GR::C), dim3(GR::NT),
+                       pcs::pencil_rows_smem<GR>(), st, pdl);
+}
+template <int S, int H, int NT>
+cudaError_t launch_pencil_planes(float2* spec, const float2* twid, int ntw, float3 iv, cudaStream_t st, bool pdl) {
+    using GP = pcs::GeoPlane<S, H, H, NT>;
+    void* args[] = {&spec, &twid, &ntw, &iv};
+    return launch_dep3(reinterpret_cast<const void*>(pcs::pd3p_plane_kernel<GP>), args, dim3(GP::M + 1), dim3(NT),
+                       GP::SMEM_BYTES, st, pdl);
+}
+template <int S, int H, int NT>
+constexpr Pencil3Entry pencil3_entry() {
+    return Pencil3Entry{S, H, H, &prepare_pencil<S, H, NT>, &launch_pencil_rows<S, H, NT>,
+                        &launch_pencil_planes<S, H, NT>};
+}
+
+const Pencil3Entry k_pencil3[] = {
+    pencil3_entry<32, 64, 1024>(),  pencil3_entry<64, 64, 1024>(),  pencil3_entry<32, 128, 1024>(),
+    pencil3_entry<64, 128, 1024>(), pencil3_entry<128, 128, 512>(), pencil3_entry<32, 256, 1024>(),
+    pencil3_entry<64, 256, 1024>(),
+};
+
 pcs_status fail3(pcs_status st, const char* what, cudaError_t e = cudaSuccess) {
     char buf[256];
     if (e != cudaSuccess) {
@@ -160,6 +225,9 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
     for (const auto& e : k_z3)
         if (e.NZ == S && e.H == H && e.W == W) ze = &e;
     if (!se || !ze) return fail3(PCS_EUNSUPPORTED, "no 3-D kernel for this volume shape");
+    const Pencil3Entry* pe = nullptr;  // the pencil form where the plane fits in shared memory
+    for (const auto& e : k_pencil3)
+        if (e.S == S && e.H == H && e.W == W) pe = &e;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const size_t n = (size_t)S * H * W;
     const size_t nspec = (size_t)S * (W / 2 + 1) * H;
@@ -208,9 +276,31 @@ pcs_status pcs_solve_volume_3d(const float* field, const unsigned char* mask, co
         a.spec = spec;
         if (ncl > S) ncl = S;
         if (ncl < 1) ncl = 1;
+        if (pe && (e = pe->prepare()) != cudaSuccess) ret = fail3(PCS_ECUDA, "pencil set-up", e);
+        // pencil form: rows (dual) -> planes -> rows (primal) -> planes; the spectrum buffer holds
+        // the planes [kx][s][y] between the launches
+        for (int it = 0; pe && it < n_iter && ret == PCS_OK; ++it) {
+            a.phase = 0;
+            a.load = it > 0;
+            a.store = 1;
+            if ((e = pe->launch_rows(a, st, it > 0)) != cudaSuccess ||
+                (e = pe->launch_planes(spec, twid, ntw, iv, st, true)) != cudaSuccess) {
+                ret = fail3(PCS_ECUDA, "launch", e);
+                break;
+            }
+            a.phase = 1;
+            a.load = 1;
+            a.store = it + 1 < n_iter;
+            if ((e = pe->launch_rows(a, st, true)) != cudaSuccess ||
+                (a.store && (e = pe->launch_planes(spec, twid, ntw, iv, st, true)) != cudaSuccess)) {
+                ret = fail3(PCS_ECUDA, "launch", e);
+                break;
+            }
+        }
+        // slice kernel and z pass (shapes whose plane does not fit in shared memory):
         // iteration n: dual step from the spectrum of chibar_n (zero at n = 0), z pass,
         // primal step, z pass (the spectrum of chibar_{n+1}; not after the last)
-        for (int it = 0; it < n_iter && ret == PCS_OK; ++it) {
+        for (int it = 0; !pe && it < n_iter && ret == PCS_OK; ++it) {
             // serpentine slice order: each launch starts on the slices the one before ended on,
             // whose state is the most likely to be still in L2
             a.phase = 0;

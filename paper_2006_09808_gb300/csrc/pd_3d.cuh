@@ -347,4 +347,203 @@ __global__ void __launch_bounds__(256) pd3_z_kernel(float2* __restrict__ spec, c
     for (int e = 0; e < EZ; ++e) __stcg(col + (size_t)(g + TZ * e) * STRIDE, x[e]);
 }
 
+// ------------------------------------------------------------------ pencil form
+// The volume's half spectrum as kx planes spec[kx][s][y], kx = 0..M (the packed DC / Nyquist
+// column split into planes 0 and M, the spectra of real rows), used where a plane fits in
+// shared memory:
+//   row kernel (no cluster): a CTA takes RPP consecutive rows of one slice; each row is read
+//       from the planes (element k of row (s, y) at spec[(k S + s) H + y]: four rows of a warp
+//       fill one 32-byte sector per k), inverse real row FFT, the dual or primal step of the
+//       row phases above, forward real row FFT of its output, stored back in place;
+//   plane kernel: one CTA per plane kx, the S x H plane in shared memory: forward y FFTs,
+//       forward z FFTs x D3 / (S H W), inverse z FFTs, inverse y FFTs.
+// One iteration = rows (dual) -> planes -> rows (primal) -> planes.
+
+// Row transport of the pencil form: a row's packed spectrum from and to the planes.
+template <class G>
+struct PlaneRows {
+    using V = typename G::V;
+    const V* in;   // planes to read; NULL: zero spectrum (the zero start)
+    V* out;        // planes to write (the same buffer: each row reads and writes only its own entries)
+    size_t row0;   // s H: slice s inside a plane
+    size_t plane;  // S H: stride between planes
+    __device__ __forceinline__ void wait() const {}
+    __device__ __forceinline__ void inverse(const Ctx<G>& cx, V* rs, int i, int g, unsigned gm, V (&x)[G::ER]) const {
+        constexpr int TR = G::TR, ER = G::ER, M = G::M;
+        if (in) {
+#pragma unroll
+            for (int e = 0; e < ER; ++e) {
+                const int k = g + TR * e;
+                const V v = __ldcg(in + (size_t)k * plane + row0 + i);
+                // k = 0: planes 0 and M hold real rows' spectra, packed as X[0] + i X[M]
+                x[e] = (k == 0) ? mk<V>(v.x, __ldcg(in + (size_t)M * plane + row0 + i).x) : v;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < ER; ++e) x[e] = mk<V>(0.f, 0.f);
+        }
+        row_unpack_inverse<G>(cx, rs, g, gm, x);
+    }
+    __device__ __forceinline__ void forward(const Ctx<G>& cx, V* rs, int i, int g, unsigned gm, V (&x)[G::ER]) const {
+        constexpr int TR = G::TR, ER = G::ER, M = G::M;
+        row_forward_pack<G>(cx, rs, g, gm, x);
+#pragma unroll
+        for (int e = 0; e < ER; ++e) {
+            const int k = g + TR * e;
+            if (k == 0) {
+                __stcg(out + row0 + i, mk<V>(x[e].x, 0.f));
+                __stcg(out + (size_t)M * plane + row0 + i, mk<V>(x[e].y, 0.f));
+            } else {
+                __stcg(out + (size_t)k * plane + row0 + i, x[e]);
+            }
+        }
+    }
+};
+
+// Shared memory of the row kernel: row scratch and twiddle tables (no spectrum columns).
+template <class G>
+constexpr size_t pencil_rows_smem() {
+    return sizeof(typename G::V) * (G::SM_ROWS + G::SM_TW + G::SM_STW_R);
+}
+
+// G: a geometry whose R equals RPP (one row pass per CTA); its C = H / RPP row tiles per
+// slice are independent CTAs, not a cluster.
+template <class G>
+__global__ void __launch_bounds__(G::NT, G::MINB) pd3p_rows_kernel(P3Params a) {
+    static_assert(G::R == G::RPP, "one row pass per CTA");
+    using V = typename G::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Ctx<G> cx;
+    cx.tbuf = nullptr;
+    cx.rows = reinterpret_cast<V*>(smem_raw);
+    cx.tw = cx.rows + G::SM_ROWS;
+    cx.stw_r = cx.tw + G::SM_TW;
+    cx.stw_c = nullptr;
+    const PDParams& prm = a.pd;
+    for (int t = threadIdx.x; t < G::NTW; t += G::NT) cx.tw[t] = prm.twid[t];
+    StageTw<G::M, G::ER>::fill(cx.stw_r, prm.twid, G::NTW / G::M, threadIdx.x, G::NT);
+    const int s = blockIdx.x / G::C;
+    cx.crank = blockIdx.x - s * G::C;  // row tile within the slice
+    __syncthreads();
+    grid_dependency_wait();  // the previous launch's planes and state complete
+    const size_t base = (size_t)s * G::H * G::W;
+    const PlaneRows<G> io{a.load ? a.spec : nullptr, a.spec, (size_t)s * G::H, (size_t)prm.S * G::H};
+    if (a.phase == 0) {
+        phase_dual<G, true, PlaneRows<G>>(cx, prm, base, prm.inv_den, true, s, io);
+    } else {
+        phase_primal<G, true, PlaneRows<G>>(cx, prm, base, !a.store, s, io);
+    }
+}
+
+// Plane kernel geometry: y transforms by groups of TYL lanes (EY elements each), z transforms
+// by groups of TZ lanes; the plane's line s (S lines of H) at pl[s H], element y at
+// P(y, 4 s); z scratch per group at stride ZP.
+template <int S_, int H_, int W_, int NT_>
+struct GeoPlane {
+    static constexpr int S = S_, H = H_, W = W_, NT = NT_, M = W / 2;
+    static constexpr int EY = default_elems(H), TYL = H / EY;
+    static constexpr int EZ = default_elems(S), TZ = S / EZ;
+    static constexpr int NGY = NT / TYL, NGZ = NT / TZ;
+    static constexpr int ZP = S + (TZ % 16);
+    static constexpr size_t PLANE = (size_t)S * H;
+    static constexpr size_t SMEM_BYTES =
+        sizeof(float2) * (PLANE + (size_t)NGZ * ZP + StageTw<H, EY>::SIZE + StageTw<S, EZ>::SIZE);
+    static_assert(SMEM_BYTES <= 232448, "the plane fits in shared memory");
+    static_assert(PLANE % 2 == 0 && (S & (S - 1)) == 0 && (H & (H - 1)) == 0 && (W & (W - 1)) == 0, "shape");
+};
+
+template <class GP>
+__global__ void __launch_bounds__(GP::NT, 1) pd3p_plane_kernel(float2* __restrict__ spec,
+                                                              const float2* __restrict__ twid, int ntw, float3 iv) {
+    constexpr int S = GP::S, H = GP::H, W = GP::W, TYL = GP::TYL, EY = GP::EY, TZ = GP::TZ, EZ = GP::EZ;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* pl = reinterpret_cast<float2*>(smem_raw);
+    float2* zs = pl + GP::PLANE;
+    float2* stw_y = zs + GP::NGZ * GP::ZP;
+    float2* stw_z = stw_y + StageTw<H, EY>::SIZE;
+    StageTw<H, EY>::fill(stw_y, twid, ntw / H, threadIdx.x, GP::NT);
+    StageTw<S, EZ>::fill(stw_z, twid, ntw / S, threadIdx.x, GP::NT);
+    const int kx = blockIdx.x;
+    float4* src = reinterpret_cast<float4*>(spec + (size_t)kx * GP::PLANE);
+    grid_dependency_wait();  // the row kernel's planes complete
+    for (int t = threadIdx.x; t < (int)GP::PLANE / 2; t += GP::NT) {
+        const float4 v = __ldcg(src + t);
+        const int idx = 2 * t, sl = idx / H, y = idx - sl * H;
+        pl[sl * H + P(y, 4 * sl)] = make_float2(v.x, v.y);
+        pl[sl * H + P(y + 1, 4 * sl)] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {  // forward y transforms
+        const int g = lane % TYL, grp = warp * (32 / TYL) + lane / TYL;
+        const unsigned gm = group_mask<TYL>(lane);
+#pragma unroll 1
+        for (int sl = grp; sl < S; sl += GP::NGY) {
+            float2* line = pl + sl * H;
+            float2 x[EY];
+#pragma unroll
+            for (int e = 0; e < EY; ++e) x[e] = line[P(g + TYL * e, 4 * sl)];
+            fft<H, TYL, false>(x, line, stw_y, g, gm, 4 * sl);
+#pragma unroll
+            for (int e = 0; e < EY; ++e) line[P(g + TYL * e, 4 * sl)] = x[e];
+            __syncwarp(gm);
+        }
+    }
+    __syncthreads();
+    {  // z pencils: forward FFT, x D3 / (S H W), inverse FFT
+        const int g = lane % TZ, grp = warp * (32 / TZ) + lane / TZ;
+        const unsigned gm = group_mask<TZ>(lane);
+        float2* zb = zs + grp * GP::ZP;
+        const float fx = (float)kx * (1.0f / (float)W) * iv.x;
+        constexpr float scale = 1.0f / ((float)S * (float)H * (float)W);
+#pragma unroll 1
+        for (int ky = grp; ky < H; ky += GP::NGZ) {
+            float2 x[EZ];
+#pragma unroll
+            for (int e = 0; e < EZ; ++e) {
+                const int sl = g + TZ * e;
+                x[e] = pl[sl * H + P(ky, 4 * sl)];
+            }
+            fft<S, TZ, false>(x, zb, stw_z, g, gm);
+            const float fy = signed_freq_pow2<H>(ky) * iv.y;
+            const float pxy = fx * fx + fy * fy;
+#pragma unroll
+            for (int e = 0; e < EZ; ++e) {
+                const float fz = signed_freq_pow2<S>(g + TZ * e) * iv.z;
+                const float k2 = pxy + fz * fz;
+                const float d = (k2 > 0.f) ? (1.0f / 3.0f - (fz * fz) / k2) * scale : 0.f;
+                x[e] = make_float2(x[e].x * d, x[e].y * d);
+            }
+            fft<S, TZ, true>(x, zb, stw_z, g, gm);
+#pragma unroll
+            for (int e = 0; e < EZ; ++e) {
+                const int sl = g + TZ * e;
+                pl[sl * H + P(ky, 4 * sl)] = x[e];
+            }
+        }
+    }
+    __syncthreads();
+    {  // inverse y transforms
+        const int g = lane % TYL, grp = warp * (32 / TYL) + lane / TYL;
+        const unsigned gm = group_mask<TYL>(lane);
+#pragma unroll 1
+        for (int sl = grp; sl < S; sl += GP::NGY) {
+            float2* line = pl + sl * H;
+            float2 x[EY];
+#pragma unroll
+            for (int e = 0; e < EY; ++e) x[e] = line[P(g + TYL * e, 4 * sl)];
+            fft<H, TYL, true>(x, line, stw_y, g, gm, 4 * sl);
+#pragma unroll
+            for (int e = 0; e < EY; ++e) line[P(g + TYL * e, 4 * sl)] = x[e];
+            __syncwarp(gm);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < (int)GP::PLANE / 2; t += GP::NT) {
+        const int idx = 2 * t, sl = idx / H, y = idx - sl * H;
+        const float2 u = pl[sl * H + P(y, 4 * sl)], w = pl[sl * H + P(y + 1, 4 * sl)];
+        __stcg(src + t, make_float4(u.x, u.y, w.x, w.y));
+    }
+}
+
 }  // namespace pcs

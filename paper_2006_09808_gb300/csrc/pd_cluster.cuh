@@ -365,26 +365,14 @@ __device__ __forceinline__ void mirror_pairs(typename G::V (&x)[G::ER], int g, u
     }
 }
 
-// Gather packed spectrum row i from the cluster and apply the inverse real
-// row transform.  Result: x[e] = W * (y[2n], y[2n+1]) for n = g + TR*e, where
-// y is the real row (the D table carries 1/(HW), so x is the true D-product).
+// Inverse real row transform of the packed spectrum row in x (element k = g + TR*e in x[e];
+// k = 0 packs X[0] + i X[M]).  Result: x[e] = W * (y[2n], y[2n+1]) for n = g + TR*e, where y
+// is the real row (the D table carries 1/(HW), so x is the true D-product).
 template <class G>
-__device__ __forceinline__ void row_inverse(const Ctx<G>& cx, typename G::V* rs, int i, int g, unsigned gm,
-                                            typename G::V (&x)[G::ER]) {
+__device__ __forceinline__ void row_unpack_inverse(const Ctx<G>& cx, typename G::V* rs, int g, unsigned gm,
+                                                   typename G::V (&x)[G::ER]) {
     using V = typename G::V;
-    constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
-    const int pi = row_slot<G>(i, g);
-#pragma unroll
-    for (int e = 0; e < ER; ++e) {
-        const int k = g + TR * e;
-        if constexpr (G::STATIC_OWNER) {
-            const int q = (TR * e) / MC;  // compile-time after unrolling
-            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + pi];
-        } else {
-            const int q = k / MC;
-            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + pi];
-        }
-    }
+    constexpr int M = G::M, TR = G::TR, NTW = G::NTW, W = G::W;
     const V* tw = cx.tw;
     mirror_pairs<G>(x, g, gm, [tw](int k, V X, V Xm) {
         if (k == 0) return mk<V>(X.x + X.y, X.x - X.y);  // X[0] = Re, X[M] = Im of the packed entry
@@ -397,14 +385,14 @@ __device__ __forceinline__ void row_inverse(const Ctx<G>& cx, typename G::V* rs,
     fft<M, TR, true>(x, rs, cx.stw_r, g, gm);
 }
 
-// Forward real row transform of z[e] = (x[2n], x[2n+1]), n = g + TR*e, and
-// scatter of the packed spectrum row i to the owners of its columns.
+// Forward real row transform of z[e] = (x[2n], x[2n+1]), n = g + TR*e, in place: the packed
+// spectrum row, element k = g + TR*e in z[e], k = 0 packing X[0] + i X[M].
 template <class G>
-__device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs, int i, int g, unsigned gm,
-                                            typename G::V (&z)[G::ER]) {
+__device__ __forceinline__ void row_forward_pack(const Ctx<G>& cx, typename G::V* rs, int g, unsigned gm,
+                                                 typename G::V (&z)[G::ER]) {
     using V = typename G::V;
     using Real = typename G::Real;
-    constexpr int M = G::M, TR = G::TR, ER = G::ER, MC = G::MC, NTW = G::NTW, W = G::W;
+    constexpr int M = G::M, TR = G::TR, NTW = G::NTW, W = G::W;
     fft<M, TR, false>(z, rs, cx.stw_r, g, gm);
     const V* tw = cx.tw;
     mirror_pairs<G>(z, g, gm, [tw](int k, V A, V Zm) {
@@ -416,6 +404,35 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
         const V w = tw[k * (NTW / W)];
         return cadd(E, cmul(w, O));
     });
+}
+
+// Gather packed spectrum row i from the cluster and apply the inverse real row transform.
+template <class G>
+__device__ __forceinline__ void row_inverse(const Ctx<G>& cx, typename G::V* rs, int i, int g, unsigned gm,
+                                            typename G::V (&x)[G::ER]) {
+    constexpr int TR = G::TR, ER = G::ER, MC = G::MC;
+    const int pi = row_slot<G>(i, g);
+#pragma unroll
+    for (int e = 0; e < ER; ++e) {
+        const int k = g + TR * e;
+        if constexpr (G::STATIC_OWNER) {
+            const int q = (TR * e) / MC;  // compile-time after unrolling
+            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + pi];
+        } else {
+            const int q = k / MC;
+            x[e] = remote_tbuf<G>(cx, q)[(k - q * MC) * G::HP + pi];
+        }
+    }
+    row_unpack_inverse<G>(cx, rs, g, gm, x);
+}
+
+// Forward real row transform of z[e] = (x[2n], x[2n+1]), n = g + TR*e, and
+// scatter of the packed spectrum row i to the owners of its columns.
+template <class G>
+__device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs, int i, int g, unsigned gm,
+                                            typename G::V (&z)[G::ER]) {
+    constexpr int TR = G::TR, ER = G::ER, MC = G::MC;
+    row_forward_pack<G>(cx, rs, g, gm, z);
     const int pi = row_slot<G>(i, g);
 #pragma unroll
     for (int e = 0; e < ER; ++e) {
@@ -431,6 +448,22 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
 }
 
 // ------------------------------------------------------------------ row phases
+
+// Row transport of the row phases: where the packed spectrum rows come from and go to.  The
+// default is the cluster's distributed spectrum columns (gather before the inverse transform,
+// scatter after the forward one, and the wait for the peers' scatters); the 3-D variant's
+// plane-major rows in global memory (pd_3d.cuh) provide the same three calls.
+template <class G>
+struct ClusterRows {
+    using V = typename G::V;
+    __device__ __forceinline__ void wait() const { cluster_wait<G::C>(); }
+    __device__ __forceinline__ void inverse(const Ctx<G>& cx, V* rs, int i, int g, unsigned gm, V (&x)[G::ER]) const {
+        row_inverse<G>(cx, rs, i, g, gm, x);
+    }
+    __device__ __forceinline__ void forward(const Ctx<G>& cx, V* rs, int i, int g, unsigned gm, V (&x)[G::ER]) const {
+        row_forward<G>(cx, rs, i, g, gm, x);
+    }
+};
 
 // Epilogue element chunk: the loads of CH elements are issued together, then
 // computed and stored (restrict-qualified pointers let the next chunk's loads
@@ -450,9 +483,9 @@ constexpr size_t SL3 = (size_t)G::H * G::W;
 // thread, or by an earlier launch; not so right after the zero start).
 // Z3 (3-D variant): q also has a z component, updated from chibar of the next
 // slice (zero difference on the last slice); s is the slice of base.
-template <class G, bool Z3 = false>
+template <class G, bool Z3 = false, class IO = ClusterRows<G>>
 __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base,
-                                           typename G::Real inv_den, bool early_cb, int s = 0) {
+                                           typename G::Real inv_den, bool early_cb, int s = 0, const IO& io = IO()) {
     using V = typename G::V;
     using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
@@ -477,13 +510,13 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
         const size_t rowoff = base + (size_t)i * W;
         const bool has_down = (i + 1 < H);
         // chibar of this row; its right neighbours come from the next lane by shuffle
-        if (pass == 0 && !early_cb) cluster_wait<G::C>();
+        if (pass == 0 && !early_cb) io.wait();
         V cb[ER];
 #pragma unroll
         for (int e = 0; e < ER; ++e) cb[e] = __ldcg(reinterpret_cast<const V*>(cbar + rowoff + 2 * (g + TR * e)));
-        if (pass == 0 && early_cb) cluster_wait<G::C>();
+        if (pass == 0 && early_cb) io.wait();
         V x[ER];
-        row_inverse<G>(cx, rs, i, g, gm, x);
+        io.inverse(cx, rs, i, g, gm, x);
         Real cr[ER];
 #pragma unroll
         for (int e = 0; e < ER; ++e) cr[e] = __shfl_sync(gm, cb[e].x, src_right);
@@ -552,7 +585,7 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
                 x[e].y = w1 * pn.y;
             }
         }
-        row_forward<G>(cx, rs, i, g, gm, x);
+        io.forward(cx, rs, i, g, gm, x);
     }
 }
 
@@ -562,9 +595,9 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
 // the dual phase) is loaded before the wait.
 // Z3 (3-D variant): G^T also takes the z differences, qz[s-1] - qz[s] with the
 // same boundary rule as the rows.
-template <class G, bool Z3 = false>
+template <class G, bool Z3 = false, class IO = ClusterRows<G>>
 __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<typename G::Real>& prm, size_t base,
-                                             bool last, int s = 0) {
+                                             bool last, int s = 0, const IO& io = IO()) {
     using V = typename G::V;
     using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
@@ -589,9 +622,9 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
         V qx[ER];
 #pragma unroll
         for (int e = 0; e < ER; ++e) qx[e] = __ldcg(reinterpret_cast<const V*>(qxp + rowoff + 2 * (g + TR * e)));
-        if (pass == 0) cluster_wait<G::C>();
+        if (pass == 0) io.wait();
         V x[ER];
-        row_inverse<G>(cx, rs, i, g, gm, x);
+        io.inverse(cx, rs, i, g, gm, x);
         Real ql[ER];
 #pragma unroll
         for (int e = 0; e < ER; ++e) ql[e] = __shfl_sync(gm, qx[e].y, src_left);
@@ -637,7 +670,7 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
                 x[e] = cb;
             }
         }
-        if (!last) row_forward<G>(cx, rs, i, g, gm, x);
+        if (!last) io.forward(cx, rs, i, g, gm, x);
     }
 }
 
