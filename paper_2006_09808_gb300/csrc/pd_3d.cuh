@@ -355,8 +355,9 @@ __global__ void __launch_bounds__(256) pd3_z_kernel(float2* __restrict__ spec, c
 //       from the planes (element k of row (s, y) at spec[(k S + s) H + y]: four rows of a warp
 //       fill one 32-byte sector per k), inverse real row FFT, the dual or primal step of the
 //       row phases above, forward real row FFT of its output, stored back in place;
-//   plane kernel: one CTA per plane kx, the S x H plane in shared memory: forward y FFTs,
-//       forward z FFTs x D3 / (S H W), inverse z FFTs, inverse y FFTs.
+//   plane kernel: one CTA per plane kx: forward y FFTs read straight from the plane, the
+//       S x H plane in shared memory for forward z FFTs x D3 / (S H W) and inverse z FFTs,
+//       inverse y FFTs written straight back.
 // One iteration = rows (dual) -> planes -> rows (primal) -> planes.
 
 // Row transport of the pencil form: a row's packed spectrum from and to the planes.
@@ -464,17 +465,12 @@ __global__ void __launch_bounds__(GP::NT, 1) pd3p_plane_kernel(float2* __restric
     StageTw<H, EY>::fill(stw_y, twid, ntw / H, threadIdx.x, GP::NT);
     StageTw<S, EZ>::fill(stw_z, twid, ntw / S, threadIdx.x, GP::NT);
     const int kx = blockIdx.x;
-    float4* src = reinterpret_cast<float4*>(spec + (size_t)kx * GP::PLANE);
+    float2* src = spec + (size_t)kx * GP::PLANE;
+    __syncthreads();  // stage twiddles
     grid_dependency_wait();  // the row kernel's planes complete
-    for (int t = threadIdx.x; t < (int)GP::PLANE / 2; t += GP::NT) {
-        const float4 v = __ldcg(src + t);
-        const int idx = 2 * t, sl = idx / H, y = idx - sl * H;
-        pl[sl * H + P(y, 4 * sl)] = make_float2(v.x, v.y);
-        pl[sl * H + P(y + 1, 4 * sl)] = make_float2(v.z, v.w);
-    }
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    {  // forward y transforms
+    {  // forward y transforms, straight from the plane in global memory (a group's lanes read
+       // consecutive entries of one line)
         const int g = lane % TYL, grp = warp * (32 / TYL) + lane / TYL;
         const unsigned gm = group_mask<TYL>(lane);
 #pragma unroll 1
@@ -482,7 +478,7 @@ __global__ void __launch_bounds__(GP::NT, 1) pd3p_plane_kernel(float2* __restric
             float2* line = pl + sl * H;
             float2 x[EY];
 #pragma unroll
-            for (int e = 0; e < EY; ++e) x[e] = line[P(g + TYL * e, 4 * sl)];
+            for (int e = 0; e < EY; ++e) x[e] = __ldcg(src + (size_t)sl * H + g + TYL * e);
             fft<H, TYL, false>(x, line, stw_y, g, gm, 4 * sl);
 #pragma unroll
             for (int e = 0; e < EY; ++e) line[P(g + TYL * e, 4 * sl)] = x[e];
@@ -496,6 +492,12 @@ __global__ void __launch_bounds__(GP::NT, 1) pd3p_plane_kernel(float2* __restric
         float2* zb = zs + grp * GP::ZP;
         const float fx = (float)kx * (1.0f / (float)W) * iv.x;
         constexpr float scale = 1.0f / ((float)S * (float)H * (float)W);
+        float fz2[EZ];  // kz^2 of this lane's elements (the same for every pencil)
+#pragma unroll
+        for (int e = 0; e < EZ; ++e) {
+            const float fz = signed_freq_pow2<S>(g + TZ * e) * iv.z;
+            fz2[e] = fz * fz;
+        }
 #pragma unroll 1
         for (int ky = grp; ky < H; ky += GP::NGZ) {
             float2 x[EZ];
@@ -509,9 +511,8 @@ __global__ void __launch_bounds__(GP::NT, 1) pd3p_plane_kernel(float2* __restric
             const float pxy = fx * fx + fy * fy;
 #pragma unroll
             for (int e = 0; e < EZ; ++e) {
-                const float fz = signed_freq_pow2<S>(g + TZ * e) * iv.z;
-                const float k2 = pxy + fz * fz;
-                const float d = (k2 > 0.f) ? (1.0f / 3.0f - (fz * fz) / k2) * scale : 0.f;
+                const float k2 = pxy + fz2[e];
+                const float d = (k2 > 0.f) ? (1.0f / 3.0f - fz2[e] / k2) * scale : 0.f;
                 x[e] = make_float2(x[e].x * d, x[e].y * d);
             }
             fft<S, TZ, true>(x, zb, stw_z, g, gm);
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(GP::NT, 1) pd3p_plane_kernel(float2* __restric
         }
     }
     __syncthreads();
-    {  // inverse y transforms
+    {  // inverse y transforms, straight back to the plane in global memory
         const int g = lane % TYL, grp = warp * (32 / TYL) + lane / TYL;
         const unsigned gm = group_mask<TYL>(lane);
 #pragma unroll 1
@@ -534,15 +535,8 @@ __global__ void __launch_bounds__(GP::NT, 1) pd3p_plane_kernel(float2* __restric
             for (int e = 0; e < EY; ++e) x[e] = line[P(g + TYL * e, 4 * sl)];
             fft<H, TYL, true>(x, line, stw_y, g, gm, 4 * sl);
 #pragma unroll
-            for (int e = 0; e < EY; ++e) line[P(g + TYL * e, 4 * sl)] = x[e];
-            __syncwarp(gm);
+            for (int e = 0; e < EY; ++e) __stcg(src + (size_t)sl * H + g + TYL * e, x[e]);
         }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < (int)GP::PLANE / 2; t += GP::NT) {
-        const int idx = 2 * t, sl = idx / H, y = idx - sl * H;
-        const float2 u = pl[sl * H + P(y, 4 * sl)], w = pl[sl * H + P(y + 1, 4 * sl)];
-        __stcg(src + t, make_float4(u.x, u.y, w.x, w.y));
     }
 }
 
