@@ -364,6 +364,9 @@ __global__ void __launch_bounds__(256) pd3_z_kernel(float2* __restrict__ spec, c
 template <class G>
 struct PlaneRows {
     using V = typename G::V;
+    // epilogue elements whose loads go out together: 2 (129.8 us per 256x256x64 iteration);
+    // 4 spills at two CTAs per SM (131.7), 4 or 8 at one CTA per SM 140.8 / 136.0
+    static constexpr int kChunkElems = 2;
     const V* in;   // planes to read; NULL: zero spectrum (the zero start)
     V* out;        // planes to write (the same buffer: each row reads and writes only its own entries)
     size_t row0;   // s H: slice s inside a plane

@@ -449,6 +449,11 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
 
 // ------------------------------------------------------------------ row phases
 
+// Epilogue element chunk: the loads of CH elements are issued together, then
+// computed and stored (restrict-qualified pointers let the next chunk's loads
+// move ahead of this chunk's stores).  2 measured fastest (1: +1.7%, 4: +3%, 8: +13%).
+constexpr int kChunk = 2;
+
 // Row transport of the row phases: where the packed spectrum rows come from and go to.  The
 // default is the cluster's distributed spectrum columns (gather before the inverse transform,
 // scatter after the forward one, and the wait for the peers' scatters); the 3-D variant's
@@ -456,6 +461,7 @@ __device__ __forceinline__ void row_forward(const Ctx<G>& cx, typename G::V* rs,
 template <class G>
 struct ClusterRows {
     using V = typename G::V;
+    static constexpr int kChunkElems = kChunk;  // epilogue elements whose loads go out together
     __device__ __forceinline__ void wait() const { cluster_wait<G::C>(); }
     __device__ __forceinline__ void inverse(const Ctx<G>& cx, V* rs, int i, int g, unsigned gm, V (&x)[G::ER]) const {
         row_inverse<G>(cx, rs, i, g, gm, x);
@@ -464,11 +470,6 @@ struct ClusterRows {
         row_forward<G>(cx, rs, i, g, gm, x);
     }
 };
-
-// Epilogue element chunk: the loads of CH elements are issued together, then
-// computed and stored (restrict-qualified pointers let the next chunk's loads
-// move ahead of this chunk's stores).  2 measured fastest (1: +1.7%, 4: +3%, 8: +13%).
-constexpr int kChunk = 2;
 
 // Elements of one slice (the 3-D variant's offset between neighbouring slices).
 template <class G>
@@ -489,7 +490,7 @@ __device__ __forceinline__ void phase_dual(const Ctx<G>& cx, const PDParamsT<typ
     using V = typename G::V;
     using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
-    constexpr int CH = (ER < kChunk) ? ER : kChunk;
+    constexpr int CH = (ER < IO::kChunkElems) ? ER : IO::kChunkElems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % TR;
     const int grp = warp * (32 / TR) + lane / TR;
@@ -601,7 +602,7 @@ __device__ __forceinline__ void phase_primal(const Ctx<G>& cx, const PDParamsT<t
     using V = typename G::V;
     using Real = typename G::Real;
     constexpr int H = G::H, W = G::W, TR = G::TR, ER = G::ER;
-    constexpr int CH = (ER < kChunk) ? ER : kChunk;
+    constexpr int CH = (ER < IO::kChunkElems) ? ER : IO::kChunkElems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane % TR;
     const int grp = warp * (32 / TR) + lane / TR;
