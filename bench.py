@@ -616,7 +616,8 @@ def run_volume3d(args):
             "config": {"workload": "3-D: the 256x256x64 volume as one unknown (3-D G and D, B0 along z), "
                                    "500 PD iterations, lambda=5e-4", "H": H, "W": W, "slices": SLICES,
                        "n_iter": N_ITER, "tau_sigma": STEP_3D, "l2": "flushed between steps (256 MiB device write)"},
-            "roofline": {"bound": "latency (L2)", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "roofline": {"bound": "latency (HBM round trips of the row kernel; the plane kernel issue- and "
+                                   "shared-pipe-bound)", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None,
                          "frac_of": "the measured HBM copy peak, in useful bytes (state, inputs and the half "
                                     "spectrum's four passes per convolution)",

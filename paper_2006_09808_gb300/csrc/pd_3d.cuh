@@ -295,7 +295,9 @@ struct GeoZ {
     static constexpr int TY = (NT / 32) * PPW;    // pencils (ky values) per tile
     static constexpr int M = W / 2;
     static constexpr int NTILES = (M + 1) * (H / TY);
-    static constexpr int NP = NZ + (TZ % 16);  // pencil buffer stride: adjacent pencils on other banks
+    // pencil buffer stride: the 32 / TZ groups of a warp write the FFT's first stage to every bank
+    // pair twice (a stride of NZ + 8 for TZ = 8 put all four groups on the same eight pairs)
+    static constexpr int NP = NZ + TZ / 2;
     static constexpr size_t SMEM_BYTES = sizeof(float2) * (TY * NP + StageTw<NZ, EZ>::SIZE);
     static_assert(H % TY == 0, "ky tiles");
     static_assert((NZ & (NZ - 1)) == 0 && (H & (H - 1)) == 0 && (W & (W - 1)) == 0,
@@ -448,7 +450,7 @@ struct GeoPlane {
     static constexpr int EY = default_elems(H), TYL = H / EY;
     static constexpr int EZ = default_elems(S), TZ = S / EZ;
     static constexpr int NGY = NT / TYL, NGZ = NT / TZ;
-    static constexpr int ZP = S + (TZ % 16);
+    static constexpr int ZP = S + TZ / 2;  // z scratch stride (see GeoZ::NP)
     static constexpr size_t PLANE = (size_t)S * H;
     static constexpr size_t SMEM_BYTES =
         sizeof(float2) * (PLANE + (size_t)NGZ * ZP + StageTw<H, EY>::SIZE + StageTw<S, EZ>::SIZE);
