@@ -51,7 +51,8 @@ def gpu3(field, mask, lam, n_iter, tv=0, weight=None, voxel=None):
 @pytest.mark.parametrize(
     "S,H,n_iter,lam,tv",
     [(32, 64, 100, 1.0, 0), (32, 64, 100, 1.0, 1), (64, 64, 60, 1e-3, 0), (32, 128, 50, 1.0, 0),
-     (128, 128, 10, 1.0, 0)],  # 128 slices: the z transform of length 128, several slices per cluster
+     (128, 128, 10, 1.0, 0),  # 128 slices: the z transform of length 128, several slices per cluster
+     (64, 128, 30, 5e-4, 0), (32, 256, 20, 5e-4, 1)],  # with the above: every pencil-form instance
 )
 def test_parity_3d(S, H, n_iter, lam, tv):
     pb = phantoms.volume(H, H, S, seed=51, lam=lam, n_iter=n_iter)
