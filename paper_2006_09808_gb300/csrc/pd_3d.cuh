@@ -1,9 +1,14 @@
 // pd_3d.cuh -- the 3-D variant: Eq. (1) with G in all three dimensions and the
 // 3-D dipole convolution of the whole volume (B0 along z, the slice axis).
 //
-// The volume's half spectrum lives in global memory between the passes of
-// one dipole convolution:
+// The volume's half spectrum lives in global memory between the passes of one dipole
+// convolution, in one of two forms (the host picks by shape):
 //
+// Pencil form (the end of this file), where a kx plane fits in shared memory: the spectrum as
+// kx planes [kx][s][y]; a cluster-free row kernel (real row FFTs and the row phases) and a
+// plane kernel (y and z FFTs with the D multiply).
+//
+// Slice form, for larger planes:
 //   slice kernel (one cluster per slice, as pd_cluster.cuh):
 //       load the slice's (ky, kx) spectrum columns, inverse column FFTs
 //       -> row phase (dual or primal step of Sec. II.A with the z terms;
@@ -18,7 +23,8 @@
 // slice kernels keep the packed DC/Nyquist column X[0] + i X[W/2] in shared
 // memory; at the global boundary it is split into its kx = 0 and kx = W/2
 // columns (each the spectrum of a real column) so that the z kernel
-// multiplies every entry by a real D.
+// multiplies every entry by a real D.  The FP64 report kernel uses the slice form's layout
+// and kernels for either form.
 #pragma once
 
 #include "pd_aux.cuh"
