@@ -84,6 +84,18 @@ def test_generic_size_rule(lib):
     assert gs(None, None, None, 1, 256, 258, 0, 0.0, 0.3, 0.3, 5, 0, None, None, None) == pcs.PCS_EINVAL  # lambda
 
 
+def test_volume_3d_shape_rule(lib):
+    """The 3-D variant's shapes (a host query, no GPU): square slices of 64, 128 and 256 with
+    32 or 64 slices, and 128 slices for 128^2 and 256^2 -- each either in the pencil form or,
+    256x256x128, in the slice form; everything else is refused."""
+    accepted = [(32, 64), (64, 64), (32, 128), (64, 128), (128, 128), (32, 256), (64, 256), (128, 256)]
+    for S, H in accepted:
+        assert lib.pcs_supported_volume_3d(S, H, H) == 1, (S, H)
+    for S, H, W in [(128, 64, 64), (16, 64, 64), (48, 128, 128), (64, 256, 128), (64, 512, 512), (64, 192, 192),
+                    (0, 64, 64)]:
+        assert lib.pcs_supported_volume_3d(S, H, W) == 0, (S, H, W)
+
+
 def test_create_without_gpu_reports_cuda_error(lib):
     import torch
 
